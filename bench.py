@@ -1,0 +1,401 @@
+"""Benchmark of the D3Q19 pseudopotential MRT step on GB300.
+
+Workload (the 256^3 throughput configuration): one periodic 256^3 box, a
+Carnahan-Starling droplet R = 40 at the centre, T = 0.7 T_c, a = 1, b = 4, R = 1,
+G = -1, s_nu = 1.0, other rates 1.1.  At this temperature the square-root
+pseudopotential needs the thermodynamic-consistency term of Eq. 16 (sigma =
+0.105 for droplets, 0.116 for flat interfaces, Sec. IV D) and the droplet the
+paper's interface width W = 5 (Eq. 59): without them the vapour density turns
+negative within ten steps, in the FP64 oracle as well.  The headline line is
+the non-orthogonal operator with FP32 arithmetic and storage; the ``forms``
+object adds both operators in FP64 and FP32 and the FP16-storage form, all on
+the same box.  A "step" is one lattice time step (psi pass + fused pass) over
+the whole box; MLUPS = 1e-6 * nodes * steps / second.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--quick]
+
+Under torchrun (N > 1) each rank runs its own box on its own GPU (replicas,
+weak scaling); the timed region is bracketed by barriers and the max over
+ranks is taken.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")  # CPU oracle leg: single-threaded numpy
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "MLUPS and % of HBM roofline per D3Q19 step (FP64 vs FP32/FP16); p50/p99 job latency"
+UNIT = "MLUPS"
+EDGE = 256
+T_OVER_TC = 0.7
+A, B, R_GAS, G = 1.0, 4.0, 1.0, -1.0
+RATES = dict(s_e=1.1, s_nu=1.0, s_q=1.1, s_pi=1.1, s_eps=1.1, s_m=1.1)
+SIGMA_DROPLET, SIGMA_FLAT = 0.105, 0.116
+W_DROPLET, W_FLAT = 5.0, 2.0
+# algorithmic bytes per node of the fused pass: 19 populations read + 19 written + psi(x) read
+FUSED_BYTES = {"f64": 19 * 8 * 2 + 8, "f32": 19 * 4 * 2 + 4, "f16": 19 * 2 * 2 + 4}
+# ... and of the psi pass: 19 populations read + psi written
+PSI_BYTES = {"f64": 19 * 8 + 8, "f32": 19 * 4 + 4, "f16": 19 * 2 + 4}
+HEADLINE = ("nonorth", "f32")
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling (200 ms) while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value, world):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def make_lattice(op, prec, edge, sigma=SIGMA_DROPLET):
+    from paper_1805_08643_gb300 import thermo
+    from paper_1805_08643_gb300.lbm import Lattice, Rates
+
+    Tc = thermo.critical_temperature(A, B, R_GAS)
+    rl, rv = thermo.coexistence_cs(T_OVER_TC, A, B, R_GAS)
+    lat = Lattice((edge,) * 3, operator=op, precision=prec, eos="cs", a=A, b=B, R=R_GAS,
+                  T=T_OVER_TC * Tc, G=G, rates=Rates(**RATES), sigma=sigma)
+    return lat, rl, rv
+
+
+def time_form(op, prec, edge, steps, warmup, world, clocks_index=None, field="droplet"):
+    """Device-timed steps of one form; returns (ms_per_step, kernel times, clocks)."""
+    import torch
+
+    lat, rl, rv = make_lattice(op, prec, edge, SIGMA_DROPLET if field == "droplet" else SIGMA_FLAT)
+    if field == "droplet":
+        lat.init_droplet((edge / 2,) * 3, 40.0 * edge / 256, W_DROPLET, rl, rv)
+    else:
+        lat.init_flat(2, edge / 4, 3 * edge / 4, W_FLAT, rl, rv)
+    lat.step(warmup)
+    lat.set_profiling(True)
+    lat.kernel_times()  # reset
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = Clocks(clocks_index) if clocks_index is not None else None
+    if clk:
+        clk.__enter__()
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    kt = lat.kernel_times()
+    status = lat.check()
+    lat.close()
+    return ms, kt, (clk.summary() if clk else None), status
+
+
+def e2e_run(op, prec, edge, steps):
+    """Through the C ABI with host buffers: H2D of the initial density, the steps, D2H of rho and u."""
+    import torch
+
+    lat, rl, rv = make_lattice(op, prec, edge)
+    from paper_1805_08643_gb300.lbm import lib
+
+    n = edge ** 3
+    rho0 = torch.empty(n, dtype=torch.float64).pin_memory()
+    # synthetic input: the same droplet as a host field (Eq. 59 profile from the seeded recipe)
+    x = np.arange(edge, dtype=np.float64)
+    d = np.minimum(np.abs(x - edge / 2), edge - np.abs(x - edge / 2))
+    r = np.sqrt(d[None, None, :] ** 2 + d[None, :, None] ** 2 + d[:, None, None] ** 2)
+    rho0.numpy()[:] = (0.5 * (rl + rv) - 0.5 * (rl - rv) * np.tanh(2.0 * (r - 40.0 * edge / 256) / W_DROPLET)).ravel()
+    rho_out = torch.empty(n, dtype=torch.float64).pin_memory()
+    u_out = torch.empty(3 * n, dtype=torch.float64).pin_memory()
+    import ctypes
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = lib.lbm_init_field(lat.handle, ctypes.c_void_p(rho0.data_ptr()), 0, rv)
+    st |= lib.lbm_step(lat.handle, steps)
+    st |= lib.lbm_moments(lat.handle, ctypes.c_void_p(rho_out.data_ptr()), ctypes.c_void_p(u_out.data_ptr()), 0)
+    t1 = time.perf_counter()
+    lat.close()
+    assert st == 0, "e2e C-ABI calls failed"
+    return t1 - t0, 8 * n, 32 * n
+
+
+def cpu_baseline(seconds_target=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    from oracle import lbm_oracle as L
+    from oracle import maxwell
+
+    nz = 8
+    grid = (EDGE, EDGE, nz)
+    Tc = L.critical_temperature(A, B, R_GAS)
+    rl, rv = maxwell.coexistence_cs(T_OVER_TC, A, B, R_GAS)
+    p = L.Params(grid=grid, operator=HEADLINE[0], a=A, b=B, R=R_GAS, T=T_OVER_TC * Tc, G=G,
+                 sigma=SIGMA_DROPLET, **RATES)
+    # the slab of the 256^3 droplet box through its centre (periodic in z)
+    rho = L.droplet_density((EDGE, EDGE, EDGE), (EDGE / 2,) * 3, 40.0, W_DROPLET, rl, rv)[EDGE // 2 - nz // 2:EDGE // 2 + nz // 2]
+    f = L.equilibrium_state(p, rho)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        f = L.step(p, f)
+        steps += 1
+        if time.perf_counter() - t0 > seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    nodes = EDGE * EDGE * nz
+    return {"value": nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{EDGE}x{EDGE}x{nz} slab through the droplet centre, {steps} FP64 steps, "
+                      f"non-orthogonal operator, single-threaded numpy"}
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    from oracle import lbm_oracle as L
+    from oracle import maxwell
+
+    nz = 4
+    grid = (EDGE, EDGE, nz)
+    Tc = L.critical_temperature(A, B, R_GAS)
+    rl, rv = maxwell.coexistence_cs(T_OVER_TC, A, B, R_GAS)
+    p = L.Params(grid=grid, operator=HEADLINE[0], a=A, b=B, R=R_GAS, T=T_OVER_TC * Tc, G=G,
+                 sigma=SIGMA_DROPLET, **RATES)
+    rho = L.droplet_density((EDGE, EDGE, EDGE), (EDGE / 2,) * 3, 40.0, W_DROPLET, rl, rv)[EDGE // 2 - nz // 2:EDGE // 2 + nz // 2]
+    f = L.equilibrium_state(p, rho)
+    for _ in range(args.warmup):
+        f = L.step(p, f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f = L.step(p, f)
+    dt = time.perf_counter() - t0
+    nodes = EDGE * EDGE * nz
+    v = nodes * args.steps / dt / 1e6
+    sample = f"each step: one FP64 oracle step of the {EDGE}x{EDGE}x{nz} slab through the droplet centre"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"D3Q19 nonorth MRT droplet {EDGE}^3 (sampled slab)",
+                                        "edge": EDGE, "T_over_Tc": T_OVER_TC},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--edge", type=int, default=EDGE)
+    ap.add_argument("--forms", default="all", help="'all' or 'headline'")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+
+    import torch
+
+    from __graft_entry__ import build
+
+    build()
+    torch.cuda.set_device(local)
+    n = args.edge ** 3
+    hbm_peak, peak_kind = peaks()
+
+    op, prec = HEADLINE
+    ms, kt, clocks, status = time_form(op, prec, args.edge, args.steps, args.warmup, world, clocks_index=local)
+    ms = max_over_ranks(ms, world)
+    ms_step = ms / args.steps
+    value = sum_over_ranks(n * args.steps / (ms / 1e3) / 1e6, world)  # all ranks' nodes / max time
+    fused_ms = kt["fused_ms"] / max(kt["fused_launches"], 1)
+    psi_ms = kt["psi_ms"] / max(kt["psi_launches"], 1)
+    achieved = FUSED_BYTES[prec] * n / (fused_ms / 1e3) / 1e9
+
+    forms = {}
+    if args.forms == "all":
+        for fop in ("nonorth", "orth"):
+            for fprec in ("f64", "f32", "f16"):
+                steps_f = max(10, args.steps // (8 if fprec == "f64" else 1))
+                fms, fkt, _, fst = time_form(fop, fprec, args.edge, steps_f, args.warmup, world)
+                f_fused = fkt["fused_ms"] / max(fkt["fused_launches"], 1)
+                f_psi = fkt["psi_ms"] / max(fkt["psi_launches"], 1)
+                step_bytes = (FUSED_BYTES[fprec] + PSI_BYTES[fprec]) * n
+                forms[f"{fop}_{fprec}_droplet"] = {
+                    "mlups": n * steps_f / (fms / 1e3) / 1e6,
+                    "ms_per_step": fms / steps_f,
+                    "fused_ms": f_fused, "psi_ms": f_psi,
+                    "fused_gbs": FUSED_BYTES[fprec] * n / (f_fused / 1e3) / 1e9,
+                    "step_gbs": step_bytes / (fms / steps_f / 1e3) / 1e9,
+                    "hbm_frac_fused": FUSED_BYTES[fprec] * n / (f_fused / 1e3) / 1e9 / hbm_peak,
+                    "bytes_per_lup_two_pass": FUSED_BYTES[fprec] + PSI_BYTES[fprec],
+                    "status": fst,
+                }
+
+        for fprec in ("f64", "f32"):
+            steps_f = max(10, args.steps // (8 if fprec == "f64" else 1))
+            fms, fkt, _, fst = time_form("nonorth", fprec, args.edge, steps_f, args.warmup, world, field="flat")
+            f_fused = fkt["fused_ms"] / max(fkt["fused_launches"], 1)
+            forms[f"nonorth_{fprec}_flat"] = {"mlups": n * steps_f / (fms / 1e3) / 1e6, "ms_per_step": fms / steps_f,
+                                             "fused_ms": f_fused,
+                                             "hbm_frac_fused": FUSED_BYTES[fprec] * n / (f_fused / 1e3) / 1e9 / hbm_peak,
+                                             "status": fst}
+
+    e2e_steps = args.steps
+    t_e2e, h2d, d2h = e2e_run(op, prec, args.edge, e2e_steps)
+    e2e_val = sum_over_ranks(n * e2e_steps / max_over_ranks(t_e2e, world) / 1e6, world)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"D3Q19 non-orthogonal MRT + CS pseudopotential, {args.edge}^3 periodic box, "
+                               f"droplet R={40.0 * args.edge / 256:g} W=5, T=0.7Tc, sigma=0.105 (Eq. 16), FP32 compute and storage",
+                   "edge": args.edge, "operator": op, "precision": prec,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (populations 1.27 GB per buffer)"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "fused force+collide+stream", "bytes_per_node": FUSED_BYTES[prec],
+                     "fused_ms": fused_ms, "psi_ms": psi_ms},
+        "clocks": clocks,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
+                "d2h_bytes_per_step": d2h / e2e_steps,
+                "note": "lbm_init_field from pinned host rho, lbm_step(K), lbm_moments to pinned host"},
+        "gpu_launches": 2 * args.steps,
+        "forms": forms,
+        "status": status,
+    }
+    if cpu:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * lbm.h -- C ABI of the GB300 D3Q19 pseudopotential MRT lattice Boltzmann library.
+ *
+ * The library advances the method of Li, Du, Fei, Luo and Yu, "Three-dimensional
+ * non-orthogonal multiple-relaxation-time lattice Boltzmann model for multiphase
+ * flows" (arXiv 1805.08643) on one CUDA device:
+ *
+ *   rho = sum_a f_a, psi(rho)                              (Eq. 6; Sec. II B; Eq. 58)
+ *   F   = -G psi(x) sum_a w_a psi(x + e_a) e_a             (Eq. 15, w = 1/6, 1/12)
+ *   u   = (sum_a e_a f_a + F/2) / rho                      (Eq. 6)
+ *   m   = M f,  m* = m - Lambda (m - m_eq) + (I - Lambda/2) S,  f* = M^-1 m*   (Eq. 4, 11-14, App. A)
+ *   f_a(x + e_a, t + 1) = f*_a(x, t), periodic box         (Eq. 5)
+ *
+ * for the non-orthogonal transformation matrix of Eq. 12 or the usual orthogonal
+ * D3Q19 matrix (d'Humieres et al., the paper's Ref. 11).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Lattice units: dt = dx = c = 1, c_s^2 = 1/3.
+ *  - Node index i = x + Nx*(y + Ny*z), x fastest; N = Nx*Ny*Nz.
+ *  - Direction a = 0..18 in the order of Eq. 2.  Population arrays are
+ *    structure-of-arrays: element (a, i) at offset a*N + i.
+ *  - Every value crossing this boundary is a double, whatever the storage
+ *    precision, except device buffers handed to lbm_bind.
+ *  - "on_device" = 1: the pointer is CUDA device memory of the context's
+ *    device; 0: host memory.  The caller owns every buffer it passes.
+ *  - Work is queued on the stream given to lbm_create.  Calls that return host
+ *    data (on_device = 0, lbm_diag, lbm_check) synchronise that stream.
+ *  - No entry point aborts or prints.  Each returns an lbm_status; the text of
+ *    the last error of a context is available from lbm_last_error.
+ *  - A context is not thread-safe: one host thread drives it at a time.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = 1,        /* invalid argument (null pointer, bad size or enum)     */
+  LBM_ERR_OOM = 2,        /* device allocation failed                             */
+  LBM_ERR_CUDA = 3,       /* a CUDA runtime call failed (detail in lbm_last_error) */
+  LBM_ERR_NONFINITE = 4,  /* a density or velocity became NaN or infinite         */
+  LBM_ERR_EOS_DOMAIN = 5, /* rho <= 0, b rho/4 >= 1 or a negative sqrt radicand   */
+  LBM_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up                   */
+  LBM_ERR_STATE = 7       /* call out of order (e.g. lbm_step before an init)     */
+} lbm_status;
+
+/* Transformation matrix: the usual orthogonal one, or Eq. 12 (Sec. II B). */
+typedef enum { LBM_OP_ORTHOGONAL = 0, LBM_OP_NONORTHOGONAL = 1 } lbm_operator;
+
+/* Pseudopotential (Sec. II B): square root of the Carnahan-Starling EOS
+ * (Eq. 58), exponential psi0*exp(-rho0/rho), or none (no interaction force). */
+typedef enum { LBM_EOS_CS = 0, LBM_EOS_EXP = 1, LBM_EOS_NONE = 2 } lbm_eos_kind;
+
+/* Arithmetic and storage of the populations.  F64: FP64 arithmetic and storage.
+ * F32: FP32 arithmetic, FP32 storage.  F32_STORE_F16: FP32 arithmetic, FP16
+ * storage.  The reduced forms store deviations f_a - w_a rho_ref (the FP16 form
+ * divides them by the lattice weight w_a) and keep the EOS and every global
+ * reduction in FP64. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F32_STORE_F16 = 2 } lbm_precision;
+
+typedef struct {
+  int kind;            /* lbm_eos_kind                                           */
+  double a, b, R, T;   /* Carnahan-Starling parameters (Eq. 58); T_c = 0.37733 a/(bR) */
+  double psi0, rho0;   /* exponential form                                       */
+} lbm_eos;
+
+/* Relaxation rates s (not times).  Non-orthogonal operator (Eq. 11): s_e for
+ * moment 4, s_nu for 5-9, s_q for 10-15, s_pi for 16-18.  Orthogonal operator:
+ * s_e (energy e), s_eps (eps), s_q (q_x, q_y, q_z), s_nu (p_xx, p_ww, p_xy,
+ * p_yz, p_xz), s_pi (pi_xx, pi_ww), s_m (m_x, m_y, m_z).  Conserved moments
+ * relax with rate 1 (Sec. II B). */
+typedef struct {
+  double s_e, s_nu, s_q, s_pi, s_eps, s_m;
+} lbm_rates;
+
+/* Create a context for a periodic Nx x Ny x Nz box (grid = {Nx, Ny, Nz}, each
+ * >= 3 so that the periodic neighbours are distinct).  G is the interaction
+ * strength of Eq. 15; sigma the constant of Eq. 16 (0 disables that term).
+ * cuda_stream is a cudaStream_t of the current device (NULL = legacy default
+ * stream).  Allocates no device memory: call lbm_bind or let the first init
+ * allocate.  Errors: LBM_ERR_ARG.  On success *out owns the context. */
+lbm_status lbm_create(const int grid[3], const lbm_eos *eos, double G,
+                      const lbm_rates *rates, int op, int precision, double sigma,
+                      void *cuda_stream, lbm_ctx **out);
+
+/* Bytes of the three device buffers a context needs: each of the two
+ * population buffers, the psi buffer, and the scratch buffer (reductions and
+ * the error word). */
+lbm_status lbm_buffer_bytes(const lbm_ctx *ctx, size_t *population_bytes,
+                            size_t *psi_bytes, size_t *scratch_bytes);
+
+/* Hand the context caller-owned device buffers of at least the sizes above,
+ * 256-byte aligned (e.g. from a PyTorch allocation).  They must outlive the
+ * context.  Without this call the first init allocates its own (LBM_ERR_OOM
+ * when that fails).  Errors: LBM_ERR_ARG, LBM_ERR_STATE (already bound). */
+lbm_status lbm_bind(lbm_ctx *ctx, void *f_a, void *f_b, void *psi, void *scratch);
+
+/* Initial state at rest, f_a = w_a rho0(x) = M^-1 m_eq(rho0, u = 0), for:
+ *  - one droplet, Eq. 59: rho0 = (rho_l + rho_v)/2 - (rho_l - rho_v)/2 tanh(2 (r - R)/W),
+ *    r the periodic minimum-image distance from centre (node coordinates 0..N-1);
+ *  - n droplets (centres: n x 3 doubles, radii: n doubles, host memory): the
+ *    pointwise maximum of their Eq. 59 profiles;
+ *  - a liquid slab between planes lo < hi across axis (0 = x, 1 = y, 2 = z):
+ *    rho0 = rho_v + (rho_l - rho_v)/2 [tanh(2 (c - lo)/W) - tanh(2 (c - hi)/W)];
+ *  - an arbitrary density field rho (N doubles), with reference density rho_ref
+ *    for the deviation storage of the reduced precisions.
+ * The droplet and slab forms take rho_ref = rho_v.  Resets the step counter.
+ * Errors: LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_init_droplet(lbm_ctx *ctx, const double centre[3], double R, double W,
+                            double rho_l, double rho_v);
+lbm_status lbm_init_droplets(lbm_ctx *ctx, int n, const double *centres, const double *radii,
+                             double W, double rho_l, double rho_v);
+lbm_status lbm_init_flat(lbm_ctx *ctx, int axis, double lo, double hi, double W,
+                         double rho_l, double rho_v);
+lbm_status lbm_init_field(lbm_ctx *ctx, const double *rho, int on_device, double rho_ref);
+
+/* Advance n >= 1 time steps (asynchronous on the context's stream).  Each step
+ * is two kernels: the psi pass and the fused force + collision + pull-streaming
+ * pass.  Errors: LBM_ERR_ARG (n < 1), LBM_ERR_STATE (no init), LBM_ERR_CUDA;
+ * LBM_ERR_EOS_DOMAIN / LBM_ERR_NONFINITE when a check interval is set (below)
+ * and a check inside this call fails. */
+lbm_status lbm_step(lbm_ctx *ctx, int n);
+
+/* Density rho (N doubles) and velocity u (3N doubles, u_x block then u_y then
+ * u_z) of the current state, Eq. 6 with the force of Eq. 15. */
+lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u, int on_device);
+
+/* The post-streaming populations f_a(x, t) of the current time t (19N doubles,
+ * SoA), and the reverse: make them the current state (keeps rho_ref). */
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device);
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
+
+/* FP64 reductions over the box (synchronises): out[0] = total mass sum rho,
+ * out[1..3] = total momentum sum rho u (Eq. 6), out[4] = max |u|. */
+lbm_status lbm_diag(lbm_ctx *ctx, double out[5]);
+
+/* Read and clear the device error word set by the kernels (synchronises):
+ * LBM_OK, LBM_ERR_EOS_DOMAIN or LBM_ERR_NONFINITE. */
+lbm_status lbm_check(lbm_ctx *ctx);
+
+/* Make lbm_step run lbm_check every k steps (0, the default, never). */
+lbm_status lbm_set_check_interval(lbm_ctx *ctx, int k);
+
+/* Per-kernel timing with CUDA events on the context's stream.  While enabled,
+ * lbm_step records an event pair around every launch; lbm_kernel_times
+ * (synchronises) returns the summed milliseconds and launch counts of the psi
+ * pass and of the fused pass since the last reset, then resets them. */
+lbm_status lbm_set_profiling(lbm_ctx *ctx, int enabled);
+lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
+                            double *ms_fused, long long *n_fused);
+
+/* Steps taken since the last init or lbm_set_populations. */
+long long lbm_step_count(const lbm_ctx *ctx);
+
+/* Release the context and any device memory it allocated itself. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Text of the last error of ctx ("" if none); ctx may be NULL. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+const char *lbm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

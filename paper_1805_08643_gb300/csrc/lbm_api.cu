@@ -1,0 +1,439 @@
+// C ABI of the library (declared in include/lbm.h): context lifetime, device
+// buffers, initial states, the time-step loop, observables and reductions.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using lbm::KParams;
+
+struct lbm_ctx {
+  KParams P{};
+  int precision = 0, op = 1;
+  bool sigma_on = false;
+  lbm::Launch L{};
+  void *g[2] = {nullptr, nullptr};
+  int cur = 0;
+  void *psi = nullptr;
+  void *scratch = nullptr;
+  bool owns = false, have_buffers = false, initialized = false, psi_valid = false;
+  long long steps = 0;
+  int check_interval = 0;
+  // profiling
+  bool profiling = false;
+  struct Rec { cudaEvent_t a, b; int kind; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, m);
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+size_t pop_bytes(const lbm_ctx *c) { return (size_t)19 * c->P.n * lbm::storage_bytes(c->precision); }
+size_t psi_bytes(const lbm_ctx *c) { return (size_t)c->P.n * lbm::psi_elem_bytes(c->precision); }
+
+unsigned *err_word(lbm_ctx *c) { return (unsigned *)((char *)c->scratch + lbm::kScratchErrOffset); }
+double *partials(lbm_ctx *c) { return (double *)((char *)c->scratch + lbm::kScratchPartialOffset); }
+double *result(lbm_ctx *c) { return (double *)((char *)c->scratch + lbm::kScratchResultOffset); }
+void *spare(lbm_ctx *c) { return c->g[c->cur ^ 1]; }
+
+lbm_status ensure_buffers(lbm_ctx *c) {
+  if (c->have_buffers) return LBM_OK;
+  void *p[4] = {nullptr, nullptr, nullptr, nullptr};
+  const size_t sz[4] = {pop_bytes(c), pop_bytes(c), psi_bytes(c), lbm::kScratchBytes};
+  for (int k = 0; k < 4; ++k) {
+    cudaError_t e = cudaMalloc(&p[k], sz[k]);
+    if (e != cudaSuccess) {
+      for (int j = 0; j < k; ++j) cudaFree(p[j]);
+      cudaGetLastError();
+      return cuda_fail(c, e, "cudaMalloc");
+    }
+  }
+  c->g[0] = p[0];
+  c->g[1] = p[1];
+  c->psi = p[2];
+  c->scratch = p[3];
+  c->owns = true;
+  c->have_buffers = true;
+  CK(cudaMemsetAsync(c->scratch, 0, lbm::kScratchBytes, c->L.stream), "cudaMemsetAsync(scratch)");
+  return LBM_OK;
+}
+
+cudaEvent_t pooled_event(lbm_ctx *c) {
+  if (c->pool_used == c->pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    c->pool.push_back(e);
+  }
+  return c->pool[c->pool_used++];
+}
+
+// Launch one kernel, bracketed by events while profiling is on.
+template <typename F>
+cudaError_t timed(lbm_ctx *c, int kind, F &&launch) {
+  if (!c->profiling) return launch();
+  cudaEvent_t a = pooled_event(c), b = pooled_event(c);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaEventRecord(a, c->L.stream);
+  cudaError_t e = launch();
+  cudaEventRecord(b, c->L.stream);
+  c->recs.push_back({a, b, kind});
+  return e;
+}
+
+lbm_status refresh_psi(lbm_ctx *c) {
+  if (c->psi_valid) return LBM_OK;
+  CK(lbm::launch_psi(c->P, c->precision, c->g[c->cur], c->psi, err_word(c), c->L), "psi kernel");
+  c->psi_valid = true;
+  return LBM_OK;
+}
+
+lbm_status finish_init(lbm_ctx *c, const double *rho_dev) {
+  CK(lbm::launch_state_from_rho(c->P, c->precision, rho_dev, c->g[c->cur], c->L), "state_from_rho kernel");
+  c->initialized = true;
+  c->psi_valid = false;
+  c->steps = 0;
+  return LBM_OK;
+}
+
+bool finite_positive(double v) { return std::isfinite(v) && v > 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *lbm_status_string(int s) {
+  switch (s) {
+    case LBM_OK: return "LBM_OK";
+    case LBM_ERR_ARG: return "LBM_ERR_ARG";
+    case LBM_ERR_OOM: return "LBM_ERR_OOM";
+    case LBM_ERR_CUDA: return "LBM_ERR_CUDA";
+    case LBM_ERR_NONFINITE: return "LBM_ERR_NONFINITE";
+    case LBM_ERR_EOS_DOMAIN: return "LBM_ERR_EOS_DOMAIN";
+    case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT";
+    case LBM_ERR_STATE: return "LBM_ERR_STATE";
+    default: return "LBM_ERR_UNKNOWN";
+  }
+}
+
+const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : ""; }
+
+lbm_status lbm_create(const int grid[3], const lbm_eos *eos, double G, const lbm_rates *rates, int op,
+                      int precision, double sigma, void *cuda_stream, lbm_ctx **out) {
+  if (!out) return LBM_ERR_ARG;
+  *out = nullptr;
+  if (!grid || !eos || !rates) return LBM_ERR_ARG;
+  if (grid[0] < 3 || grid[1] < 3 || grid[2] < 3) return LBM_ERR_ARG;
+  const long long n = (long long)grid[0] * grid[1] * grid[2];
+  if (n >= (1LL << 31) || grid[2] > 65535) return LBM_ERR_ARG;  // 32-bit node index; grid.z
+  if (op != LBM_OP_ORTHOGONAL && op != LBM_OP_NONORTHOGONAL) return LBM_ERR_ARG;
+  if (precision < LBM_F64 || precision > LBM_F32_STORE_F16) return LBM_ERR_ARG;
+  if (eos->kind < LBM_EOS_CS || eos->kind > LBM_EOS_NONE) return LBM_ERR_ARG;
+  const double rs[6] = {rates->s_e, rates->s_nu, rates->s_q, rates->s_pi, rates->s_eps, rates->s_m};
+  for (double s : rs)
+    if (!(s > 0.0 && s < 2.0)) return LBM_ERR_ARG;  // stable range of a relaxation rate
+  if (!std::isfinite(G) || !std::isfinite(sigma)) return LBM_ERR_ARG;
+  if (eos->kind == LBM_EOS_CS) {
+    if (!finite_positive(eos->b) || !finite_positive(eos->R) || !finite_positive(eos->T) ||
+        !std::isfinite(eos->a) || G == 0.0)
+      return LBM_ERR_ARG;
+  } else if (eos->kind == LBM_EOS_EXP) {
+    if (!std::isfinite(eos->psi0) || !finite_positive(eos->rho0)) return LBM_ERR_ARG;
+  }
+  if (sigma != 0.0 && eos->kind == LBM_EOS_NONE) return LBM_ERR_ARG;
+
+  lbm_ctx *c = new (std::nothrow) lbm_ctx();
+  if (!c) return LBM_ERR_OOM;
+  KParams &P = c->P;
+  P.nx = grid[0];
+  P.ny = grid[1];
+  P.nz = grid[2];
+  P.n = (int)n;
+  P.G = eos->kind == LBM_EOS_NONE ? 0.0 : G;
+  P.rho_ref = 0.0;
+  P.s_e = rates->s_e;
+  P.s_nu = rates->s_nu;
+  P.s_q = rates->s_q;
+  P.s_pi = rates->s_pi;
+  P.s_eps = rates->s_eps;
+  P.s_m = rates->s_m;
+  P.sigma_coef = 6.0 * sigma * G * G / (1.0 / rates->s_e - 0.5);
+  P.eos = eos->kind;
+  P.a = eos->a;
+  P.b = eos->b;
+  P.RT = eos->R * eos->T;
+  P.psi0 = eos->psi0;
+  P.rho0 = eos->rho0;
+  c->precision = precision;
+  c->op = op;
+  c->sigma_on = sigma != 0.0;
+  c->L.stream = (cudaStream_t)cuda_stream;
+  c->L.bx = 32;
+  c->L.by = 4;
+  *out = c;
+  return LBM_OK;
+}
+
+lbm_status lbm_buffer_bytes(const lbm_ctx *c, size_t *pb, size_t *sb, size_t *xb) {
+  if (!c) return LBM_ERR_ARG;
+  if (pb) *pb = pop_bytes(c);
+  if (sb) *sb = psi_bytes(c);
+  if (xb) *xb = lbm::kScratchBytes;
+  return LBM_OK;
+}
+
+lbm_status lbm_bind(lbm_ctx *c, void *fa, void *fb, void *psi, void *scratch) {
+  if (!c) return LBM_ERR_ARG;
+  if (c->have_buffers) return fail(c, LBM_ERR_STATE, "buffers already bound or allocated");
+  if (!fa || !fb || !psi || !scratch || fa == fb) return fail(c, LBM_ERR_ARG, "null or aliased buffer");
+  for (void *p : {fa, fb, psi, scratch})
+    if (((uintptr_t)p & 255u) != 0) return fail(c, LBM_ERR_ARG, "buffers must be 256-byte aligned");
+  c->g[0] = fa;
+  c->g[1] = fb;
+  c->psi = psi;
+  c->scratch = scratch;
+  c->owns = false;
+  c->have_buffers = true;
+  CK(cudaMemsetAsync(c->scratch, 0, lbm::kScratchBytes, c->L.stream), "cudaMemsetAsync(scratch)");
+  return LBM_OK;
+}
+
+lbm_status lbm_init_droplets(lbm_ctx *c, int n, const double *centres, const double *radii, double W,
+                             double rho_l, double rho_v) {
+  if (!c || n < 1 || !centres || !radii) return fail(c, LBM_ERR_ARG, "bad droplet list");
+  if (!finite_positive(W) || !finite_positive(rho_l) || !finite_positive(rho_v))
+    return fail(c, LBM_ERR_ARG, "W, rho_l and rho_v must be positive");
+  for (int k = 0; k < n; ++k)
+    if (!std::isfinite(centres[3 * k]) || !std::isfinite(centres[3 * k + 1]) ||
+        !std::isfinite(centres[3 * k + 2]) || !(radii[k] >= 0.0))
+      return fail(c, LBM_ERR_ARG, "bad droplet centre or radius");
+  lbm_status s = ensure_buffers(c);
+  if (s != LBM_OK) return s;
+  c->P.rho_ref = rho_v;
+  double *rho = (double *)spare(c);
+  for (int k0 = 0; k0 < n; k0 += lbm::kDropletChunk) {
+    lbm::DropletChunk ch{};
+    ch.count = std::min(lbm::kDropletChunk, n - k0);
+    for (int k = 0; k < ch.count; ++k) {
+      ch.cx[k] = centres[3 * (k0 + k)];
+      ch.cy[k] = centres[3 * (k0 + k) + 1];
+      ch.cz[k] = centres[3 * (k0 + k) + 2];
+      ch.r[k] = radii[k0 + k];
+    }
+    CK(lbm::launch_rho_droplets(c->P, rho, ch, W, rho_l, rho_v, k0 == 0, c->L), "rho_droplets kernel");
+  }
+  return finish_init(c, rho);
+}
+
+lbm_status lbm_init_droplet(lbm_ctx *c, const double centre[3], double R, double W, double rho_l,
+                            double rho_v) {
+  if (!c || !centre) return fail(c, LBM_ERR_ARG, "null argument");
+  return lbm_init_droplets(c, 1, centre, &R, W, rho_l, rho_v);
+}
+
+lbm_status lbm_init_flat(lbm_ctx *c, int axis, double lo, double hi, double W, double rho_l, double rho_v) {
+  if (!c || axis < 0 || axis > 2 || !(lo < hi) || !std::isfinite(lo) || !std::isfinite(hi))
+    return fail(c, LBM_ERR_ARG, "bad slab geometry");
+  if (!finite_positive(W) || !finite_positive(rho_l) || !finite_positive(rho_v))
+    return fail(c, LBM_ERR_ARG, "W, rho_l and rho_v must be positive");
+  lbm_status s = ensure_buffers(c);
+  if (s != LBM_OK) return s;
+  c->P.rho_ref = rho_v;
+  double *rho = (double *)spare(c);
+  CK(lbm::launch_rho_slab(c->P, rho, axis, lo, hi, W, rho_l, rho_v, c->L), "rho_slab kernel");
+  return finish_init(c, rho);
+}
+
+lbm_status lbm_init_field(lbm_ctx *c, const double *rho, int on_device, double rho_ref) {
+  if (!c || !rho || !std::isfinite(rho_ref)) return fail(c, LBM_ERR_ARG, "null field or bad rho_ref");
+  lbm_status s = ensure_buffers(c);
+  if (s != LBM_OK) return s;
+  c->P.rho_ref = rho_ref;
+  const double *src = rho;
+  if (!on_device) {
+    double *tmp = (double *)spare(c);
+    CK(cudaMemcpyAsync(tmp, rho, sizeof(double) * c->P.n, cudaMemcpyHostToDevice, c->L.stream),
+       "cudaMemcpyAsync(rho H2D)");
+    src = tmp;
+  }
+  s = finish_init(c, src);
+  if (s != LBM_OK) return s;
+  if (!on_device) CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
+  return LBM_OK;
+}
+
+lbm_status lbm_check(lbm_ctx *c) {
+  if (!c) return LBM_ERR_ARG;
+  if (!c->have_buffers) return LBM_OK;
+  unsigned w = 0;
+  CK(cudaMemcpyAsync(&w, err_word(c), sizeof(unsigned), cudaMemcpyDeviceToHost, c->L.stream), "read error word");
+  CK(cudaMemsetAsync(err_word(c), 0, sizeof(unsigned), c->L.stream), "clear error word");
+  CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
+  if (w & lbm::kErrNonFinite) return fail(c, LBM_ERR_NONFINITE, "non-finite density");
+  if (w & lbm::kErrEosDomain) return fail(c, LBM_ERR_EOS_DOMAIN, "density left the domain of the EOS");
+  return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *c, int n) {
+  if (!c) return LBM_ERR_ARG;
+  if (n < 1) return fail(c, LBM_ERR_ARG, "n must be >= 1");
+  if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_step before an init");
+  for (int k = 0; k < n; ++k) {
+    void *gin = c->g[c->cur], *gout = c->g[c->cur ^ 1];
+    CK(timed(c, 0, [&] { return lbm::launch_psi(c->P, c->precision, gin, c->psi, err_word(c), c->L); }),
+       "psi kernel");
+    CK(timed(c, 1, [&] {
+         return lbm::launch_fused(c->P, c->precision, c->op, c->sigma_on, gin, gout, c->psi, c->L);
+       }),
+       "fused kernel");
+    c->cur ^= 1;
+    c->psi_valid = false;
+    ++c->steps;
+    if (c->check_interval > 0 && c->steps % c->check_interval == 0) {
+      lbm_status s = lbm_check(c);
+      if (s != LBM_OK) return s;
+    }
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx *c, double *rho, double *u, int on_device) {
+  if (!c || (!rho && !u)) return fail(c, LBM_ERR_ARG, "no output");
+  if (!c->initialized) return fail(c, LBM_ERR_STATE, "no state");
+  lbm_status s = refresh_psi(c);
+  if (s != LBM_OK) return s;
+  const size_t n = c->P.n;
+  if (on_device) {
+    CK(lbm::launch_moments(c->P, c->precision, c->g[c->cur], c->psi, rho, u, c->L), "moments kernel");
+    return LBM_OK;
+  }
+  double *tmp = (double *)spare(c);  // 4N doubles fit in any population buffer
+  CK(lbm::launch_moments(c->P, c->precision, c->g[c->cur], c->psi, tmp, tmp + n, c->L), "moments kernel");
+  if (rho) CK(cudaMemcpyAsync(rho, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->L.stream), "D2H rho");
+  if (u) CK(cudaMemcpyAsync(u, tmp + n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->L.stream), "D2H u");
+  CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
+  return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx *c, double *f, int on_device) {
+  if (!c || !f) return fail(c, LBM_ERR_ARG, "null output");
+  if (!c->initialized) return fail(c, LBM_ERR_STATE, "no state");
+  const size_t n = c->P.n;
+  if (on_device) {
+    CK(lbm::launch_get_populations(c->P, c->precision, c->g[c->cur], f, 0, 19, c->L), "get_populations kernel");
+    return LBM_OK;
+  }
+  double *tmp = (double *)spare(c);
+  for (int a = 0; a < 19; ++a) {
+    CK(lbm::launch_get_populations(c->P, c->precision, c->g[c->cur], tmp, a, a + 1, c->L),
+       "get_populations kernel");
+    CK(cudaMemcpyAsync(f + a * n, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->L.stream), "D2H f");
+    CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx *c, const double *f, int on_device) {
+  if (!c || !f) return fail(c, LBM_ERR_ARG, "null input");
+  if (!c->initialized) return fail(c, LBM_ERR_STATE, "set_populations needs an init (for rho_ref)");
+  const size_t n = c->P.n;
+  if (on_device) {
+    CK(lbm::launch_set_populations(c->P, c->precision, f, c->g[c->cur], 0, 19, c->L), "set_populations kernel");
+  } else {
+    double *tmp = (double *)spare(c);
+    for (int a = 0; a < 19; ++a) {
+      CK(cudaMemcpyAsync(tmp, f + a * n, sizeof(double) * n, cudaMemcpyHostToDevice, c->L.stream), "H2D f");
+      CK(lbm::launch_set_populations(c->P, c->precision, tmp, c->g[c->cur], a, a + 1, c->L),
+         "set_populations kernel");
+      CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
+    }
+  }
+  c->psi_valid = false;
+  c->steps = 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_diag(lbm_ctx *c, double out[5]) {
+  if (!c || !out) return fail(c, LBM_ERR_ARG, "null output");
+  if (!c->initialized) return fail(c, LBM_ERR_STATE, "no state");
+  lbm_status s = refresh_psi(c);
+  if (s != LBM_OK) return s;
+  CK(lbm::launch_diag(c->P, c->precision, c->g[c->cur], c->psi, partials(c), result(c), c->L), "diag kernels");
+  CK(cudaMemcpyAsync(out, result(c), 5 * sizeof(double), cudaMemcpyDeviceToHost, c->L.stream), "D2H diag");
+  CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
+  return LBM_OK;
+}
+
+lbm_status lbm_set_check_interval(lbm_ctx *c, int k) {
+  if (!c || k < 0) return LBM_ERR_ARG;
+  c->check_interval = k;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_profiling(lbm_ctx *c, int enabled) {
+  if (!c) return LBM_ERR_ARG;
+  c->profiling = enabled != 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_kernel_times(lbm_ctx *c, double *ms_psi, long long *n_psi, double *ms_fused, long long *n_fused) {
+  if (!c) return LBM_ERR_ARG;
+  CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
+  double t[2] = {0, 0};
+  long long cnt[2] = {0, 0};
+  for (auto &r : c->recs) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b), "cudaEventElapsedTime");
+    t[r.kind] += ms;
+    cnt[r.kind] += 1;
+  }
+  c->recs.clear();
+  c->pool_used = 0;
+  if (ms_psi) *ms_psi = t[0];
+  if (n_psi) *n_psi = cnt[0];
+  if (ms_fused) *ms_fused = t[1];
+  if (n_fused) *n_fused = cnt[1];
+  return LBM_OK;
+}
+
+long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
+
+void lbm_destroy(lbm_ctx *c) {
+  if (!c) return;
+  if (c->have_buffers || !c->pool.empty()) cudaStreamSynchronize(c->L.stream);
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  if (c->owns) {
+    cudaFree(c->g[0]);
+    cudaFree(c->g[1]);
+    cudaFree(c->psi);
+    cudaFree(c->scratch);
+  }
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,78 @@
+// Internal interface between the C ABI (lbm_api.cu) and the kernels
+// (lbm_kernels.cu).  Not installed; not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+enum Precision { kF64 = 0, kF32 = 1, kF16 = 2 };
+enum Operator { kOrth = 0, kNonOrth = 1 };
+enum EosKind { kEosCS = 0, kEosExp = 1, kEosNone = 2 };
+
+// Error bits the kernels set in the device error word.
+enum : unsigned { kErrEosDomain = 1u, kErrNonFinite = 2u };
+
+// Everything a kernel needs about the box and the physics, passed by value.
+struct KParams {
+  int nx, ny, nz;
+  int n;             // nx * ny * nz (< 2^31)
+  double G;          // interaction strength, Eq. 15
+  double rho_ref;    // reference density of the deviation storage
+  // relaxation rates (see lbm_rates in lbm.h)
+  double s_e, s_nu, s_q, s_pi, s_eps, s_m;
+  // Eq. 16 coefficient: the extra S_4 is sigma_coef * |sum_a w_a psi(x+e_a) e_a|^2
+  // (= 6 sigma |F|^2 / (psi^2 (1/s_e - 1/2)) with F = -G psi sum(...)).
+  double sigma_coef;
+  // equation of state
+  int eos;
+  double a, b, RT;   // Carnahan-Starling (Eq. 58), RT = R * T
+  double psi0, rho0; // exponential pseudopotential
+};
+
+// Layout of the scratch buffer.
+constexpr int kReduceBlocks = 1024;
+constexpr size_t kScratchErrOffset = 0;      // unsigned error word
+constexpr size_t kScratchPartialOffset = 256;  // kReduceBlocks x 5 doubles
+constexpr size_t kScratchResultOffset = kScratchPartialOffset + sizeof(double) * 5 * kReduceBlocks;
+constexpr size_t kScratchBytes = kScratchResultOffset + 256;
+
+// Droplets handed to the density-field kernel in chunks.
+constexpr int kDropletChunk = 64;
+struct DropletChunk {
+  int count;
+  double cx[kDropletChunk], cy[kDropletChunk], cz[kDropletChunk], r[kDropletChunk];
+};
+
+struct Launch {
+  cudaStream_t stream;
+  int bx, by;  // thread-block shape (x, y) of the per-node kernels
+};
+
+size_t storage_bytes(int precision);  // bytes per stored population
+size_t psi_elem_bytes(int precision);
+
+// One time step is launch_psi followed by launch_fused (buffers swapped by the caller).
+cudaError_t launch_psi(const KParams &P, int precision, const void *g, void *psi,
+                       unsigned *err, const Launch &L);
+cudaError_t launch_fused(const KParams &P, int precision, int op, bool sigma,
+                         const void *g_in, void *g_out, const void *psi, const Launch &L);
+
+cudaError_t launch_moments(const KParams &P, int precision, const void *g, const void *psi,
+                           double *rho, double *u, const Launch &L);
+cudaError_t launch_diag(const KParams &P, int precision, const void *g, const void *psi,
+                        double *partials, double *result, const Launch &L);
+
+cudaError_t launch_rho_droplets(const KParams &P, double *rho, const DropletChunk &chunk,
+                                double W, double rho_l, double rho_v, bool first, const Launch &L);
+cudaError_t launch_rho_slab(const KParams &P, double *rho, int axis, double lo, double hi,
+                            double W, double rho_l, double rho_v, const Launch &L);
+cudaError_t launch_state_from_rho(const KParams &P, int precision, const double *rho, void *g,
+                                  const Launch &L);
+cudaError_t launch_get_populations(const KParams &P, int precision, const void *g, double *out,
+                                   int a_lo, int a_hi, const Launch &L);
+cudaError_t launch_set_populations(const KParams &P, int precision, const double *f, void *g,
+                                   int a_lo, int a_hi, const Launch &L);
+
+}  // namespace lbm

@@ -1,0 +1,395 @@
+// Kernels of the D3Q19 pseudopotential MRT step and their launchers.
+//
+// State layout: the stored buffer g holds, per direction a (SoA, a*N + i),
+// the deviation of the post-collision population f*_a(x, t-1) from
+// w_a rho_ref.  The post-streaming population of time t is pulled:
+// f_a(x, t) = g_a(x - e_a) (Eq. 5).  One step is
+//   psi pass:   rho(x,t) = sum_a f_a(x,t) -> psi(x)               (Eq. 6, EOS)
+//   fused pass: pull f, F from psi (Eq. 15), u (Eq. 6), collide in moment
+//               space (Eq. 4), store f*(x, t) at x into the other buffer.
+#include <cuda_fp16.h>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+size_t storage_bytes(int precision) {
+  return precision == kF64 ? 8 : (precision == kF32 ? 4 : 2);
+}
+size_t psi_elem_bytes(int precision) { return precision == kF64 ? 8 : 4; }
+
+namespace {
+
+template <int P> struct Types;
+template <> struct Types<kF64> { using S = double; using T = double; using Psi = double; };
+template <> struct Types<kF32> { using S = float; using T = float; using Psi = float; };
+template <> struct Types<kF16> { using S = __half; using T = float; using Psi = float; };
+
+__device__ __forceinline__ bool node_of_thread(const KParams &P, int &x, int &y, int &z) {
+  x = blockIdx.x * blockDim.x + threadIdx.x;
+  y = blockIdx.y * blockDim.y + threadIdx.y;
+  z = blockIdx.z;
+  return x < P.nx && y < P.ny;
+}
+
+// ------------------------------------------------------------------ psi pass
+template <int PREC, int EOS>
+__global__ void __launch_bounds__(256) psi_kernel(const typename Types<PREC>::S *__restrict__ g,
+                                                  typename Types<PREC>::Psi *__restrict__ psi,
+                                                  const KParams P, unsigned *__restrict__ err) {
+  using S = typename Types<PREC>::S;
+  using T = typename Types<PREC>::T;
+  int x, y, z;
+  if (!node_of_thread(P, x, y, z)) return;
+  const Nbhd nb(x, y, z, P);
+  T f[19];
+  pull<S, T>(g, P.n, nb, f);
+  // sum in the order of the forward chain: rest + axis pairs + diagonal pairs
+  const T sax = (f[1] + f[2]) + (f[3] + f[4]) + (f[5] + f[6]);
+  const T sdg = ((f[7] + f[8]) + (f[9] + f[10])) + ((f[11] + f[12]) + (f[13] + f[14])) +
+                ((f[15] + f[16]) + (f[17] + f[18]));
+  const T drho = f[0] + sax + sdg;
+  unsigned e = 0;
+  const double v = eos_psi<EOS>(P.rho_ref + (double)drho, P, e);
+  psi[nb.self] = (typename Types<PREC>::Psi)v;
+  if (e) atomicOr(err, e);
+}
+
+// ------------------------------------------------------------------ fused pass
+template <int PREC, int OP, bool SIGMA>
+__global__ void __launch_bounds__(256) fused_kernel(const typename Types<PREC>::S *__restrict__ g_in,
+                                                    typename Types<PREC>::S *__restrict__ g_out,
+                                                    const typename Types<PREC>::Psi *__restrict__ psi,
+                                                    const KParams P) {
+  using S = typename Types<PREC>::S;
+  using T = typename Types<PREC>::T;
+  int x, y, z;
+  if (!node_of_thread(P, x, y, z)) return;
+  const Nbhd nb(x, y, z, P);
+  T f[19];
+  pull<S, T>(g_in, P.n, nb, f);
+  // interaction force, Eq. 15
+  T p[19];
+#pragma unroll
+  for (int a = 1; a < 19; ++a) p[a] = (T)__ldg(psi + nb.dst(a));
+  p[0] = (T)__ldg(psi + nb.self);
+  T Sx, Sy, Sz;
+  psi_gradient<T>(p, Sx, Sy, Sz);
+  const T mG = (T)(-P.G);
+  const T Fx = mG * p[0] * Sx, Fy = mG * p[0] * Sy, Fz = mG * p[0] * Sz;
+  // Eq. 16: 6 sigma |F|^2 / (psi^2 (1/s_e - 1/2)) = sigma_coef |S|^2
+  const T dS4 = SIGMA ? (T)P.sigma_coef * (Sx * Sx + Sy * Sy + Sz * Sz) : T(0);
+  const Rates<T> r(P);
+  if (OP == kNonOrth)
+    collide_nonorth<T>(f, (T)P.rho_ref, Fx, Fy, Fz, dS4, r);
+  else
+    collide_orth<T>(f, (T)P.rho_ref, Fx, Fy, Fz, dS4, r);
+#pragma unroll
+  for (int a = 0; a < 19; ++a) Storage<S>::store(g_out + (size_t)a * P.n + nb.self, a, f[a]);
+}
+
+// ------------------------------------------------------------------ observables
+// rho and u (Eq. 6) of the current state, in FP64 whatever the storage.
+template <int PREC>
+__device__ __forceinline__ void node_moments(const typename Types<PREC>::S *__restrict__ g,
+                                             const typename Types<PREC>::Psi *__restrict__ psi,
+                                             const KParams &P, const Nbhd &nb, double &rho,
+                                             double &rux, double &ruy, double &ruz) {
+  using S = typename Types<PREC>::S;
+  double f[19];
+  pull<S, double>(g, P.n, nb, f);
+  double drho = 0, jx = 0, jy = 0, jz = 0;
+  const int ex[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+  const int ey[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+  const int ez[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    drho += f[a];
+    jx += ex[a] * f[a];
+    jy += ey[a] * f[a];
+    jz += ez[a] * f[a];
+  }
+  double p[19];
+#pragma unroll
+  for (int a = 1; a < 19; ++a) p[a] = (double)psi[nb.dst(a)];
+  p[0] = (double)psi[nb.self];
+  double Sx, Sy, Sz;
+  psi_gradient<double>(p, Sx, Sy, Sz);
+  const double k = -P.G * p[0];
+  rho = P.rho_ref + drho;
+  rux = jx + 0.5 * k * Sx;
+  ruy = jy + 0.5 * k * Sy;
+  ruz = jz + 0.5 * k * Sz;
+}
+
+template <int PREC>
+__global__ void moments_kernel(const typename Types<PREC>::S *__restrict__ g,
+                               const typename Types<PREC>::Psi *__restrict__ psi, const KParams P,
+                               double *__restrict__ rho_out, double *__restrict__ u_out) {
+  int x, y, z;
+  if (!node_of_thread(P, x, y, z)) return;
+  const Nbhd nb(x, y, z, P);
+  double rho, rux, ruy, ruz;
+  node_moments<PREC>(g, psi, P, nb, rho, rux, ruy, ruz);
+  if (rho_out) rho_out[nb.self] = rho;
+  if (u_out) {
+    u_out[nb.self] = rux / rho;
+    u_out[(size_t)P.n + nb.self] = ruy / rho;
+    u_out[2 * (size_t)P.n + nb.self] = ruz / rho;
+  }
+}
+
+// Block-partial FP64 sums of (rho, rho u) and max |u|, grid-stride over nodes,
+// then one block folds the partials in a fixed order (deterministic).
+template <int PREC>
+__global__ void __launch_bounds__(256) diag_partial_kernel(const typename Types<PREC>::S *__restrict__ g,
+                                                           const typename Types<PREC>::Psi *__restrict__ psi,
+                                                           const KParams P, double *__restrict__ partials) {
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const int x = i % P.nx, yz = i / P.nx, y = yz % P.ny, z = yz / P.ny;
+    const Nbhd nb(x, y, z, P);
+    double rho, rux, ruy, ruz;
+    node_moments<PREC>(g, psi, P, nb, rho, rux, ruy, ruz);
+    acc[0] += rho;
+    acc[1] += rux;
+    acc[2] += ruy;
+    acc[3] += ruz;
+    const double u = sqrt(rux * rux + ruy * ruy + ruz * ruz) / rho;
+    acc[4] = (u > acc[4] || u != u) ? u : acc[4];
+  }
+  __shared__ double red[5][256];
+#pragma unroll
+  for (int k = 0; k < 5; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + s];
+      const double a = red[4][threadIdx.x], b = red[4][threadIdx.x + s];
+      red[4][threadIdx.x] = (b > a || b != b) ? b : a;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 5; ++k) partials[blockIdx.x * 5 + k] = red[k][0];
+}
+
+__global__ void diag_final_kernel(const double *__restrict__ partials, int nblocks,
+                                  double *__restrict__ result) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int b = 0; b < nblocks; ++b) {
+    for (int k = 0; k < 4; ++k) acc[k] += partials[b * 5 + k];
+    const double u = partials[b * 5 + 4];
+    acc[4] = (u > acc[4] || u != u) ? u : acc[4];
+  }
+  for (int k = 0; k < 5; ++k) result[k] = acc[k];
+}
+
+// ------------------------------------------------------------------ initial state
+__device__ __forceinline__ double min_image(double d, int n) {
+  d = fabs(d);
+  return fmin(d, (double)n - d);
+}
+
+// Eq. 59 for each droplet of the chunk; several droplets combine by maximum.
+__global__ void rho_droplets_kernel(double *__restrict__ rho, const KParams P, const DropletChunk C,
+                                    double W, double rho_l, double rho_v, int first) {
+  int x, y, z;
+  if (!node_of_thread(P, x, y, z)) return;
+  const int i = x + P.nx * (y + P.ny * z);
+  double best = first ? -1e300 : rho[i];
+  for (int k = 0; k < C.count; ++k) {
+    const double dx = min_image(x - C.cx[k], P.nx), dy = min_image(y - C.cy[k], P.ny);
+    const double dz = min_image(z - C.cz[k], P.nz);
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    const double v = 0.5 * (rho_l + rho_v) - 0.5 * (rho_l - rho_v) * tanh(2.0 * (r - C.r[k]) / W);
+    best = fmax(best, v);
+  }
+  rho[i] = best;
+}
+
+// Liquid slab between planes lo and hi across one axis (Sec. IV D).
+__global__ void rho_slab_kernel(double *__restrict__ rho, const KParams P, int axis, double lo,
+                                double hi, double W, double rho_l, double rho_v) {
+  int x, y, z;
+  if (!node_of_thread(P, x, y, z)) return;
+  const double c = axis == 0 ? x : (axis == 1 ? y : z);
+  rho[x + P.nx * (y + P.ny * z)] =
+      rho_v + 0.5 * (rho_l - rho_v) * (tanh(2.0 * (c - lo) / W) - tanh(2.0 * (c - hi) / W));
+}
+
+// f_a(x, 0) = w_a rho0(x): store g_a(y) = w_a (rho0(y + e_a) - rho_ref).
+template <int PREC>
+__global__ void state_from_rho_kernel(const double *__restrict__ rho, typename Types<PREC>::S *__restrict__ g,
+                                      const KParams P) {
+  using S = typename Types<PREC>::S;
+  int x, y, z;
+  if (!node_of_thread(P, x, y, z)) return;
+  const Nbhd nb(x, y, z, P);
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    const double v = lattice_w(a) * (rho[nb.dst(a)] - P.rho_ref);
+    Storage<S>::store(g + (size_t)a * P.n + nb.self, a, (typename Types<PREC>::T)v);
+  }
+}
+
+// out[(a - a_lo) N + i] = f_a(x_i, t) for a in [a_lo, a_hi).
+template <int PREC>
+__global__ void get_populations_kernel(const typename Types<PREC>::S *__restrict__ g, double *__restrict__ out,
+                                       const KParams P, int a_lo, int a_hi) {
+  using S = typename Types<PREC>::S;
+  int x, y, z;
+  if (!node_of_thread(P, x, y, z)) return;
+  const Nbhd nb(x, y, z, P);
+#pragma unroll
+  for (int a = 0; a < 19; ++a)
+    if (a >= a_lo && a < a_hi)
+      out[(size_t)(a - a_lo) * P.n + nb.self] =
+          lattice_w(a) * P.rho_ref + (double)Storage<S>::load(g + (size_t)a * P.n + nb.src(a), a);
+}
+
+// Reverse of the above: g_a(y) = f_a(y + e_a) - w_a rho_ref.
+template <int PREC>
+__global__ void set_populations_kernel(const double *__restrict__ f, typename Types<PREC>::S *__restrict__ g,
+                                       const KParams P, int a_lo, int a_hi) {
+  using S = typename Types<PREC>::S;
+  int x, y, z;
+  if (!node_of_thread(P, x, y, z)) return;
+  const Nbhd nb(x, y, z, P);
+#pragma unroll
+  for (int a = 0; a < 19; ++a)
+    if (a >= a_lo && a < a_hi) {
+      const double v = f[(size_t)(a - a_lo) * P.n + nb.dst(a)] - lattice_w(a) * P.rho_ref;
+      Storage<S>::store(g + (size_t)a * P.n + nb.self, a, (typename Types<PREC>::T)v);
+    }
+}
+
+dim3 node_grid(const KParams &P, const Launch &L) {
+  return dim3((P.nx + L.bx - 1) / L.bx, (P.ny + L.by - 1) / L.by, P.nz);
+}
+
+template <int PREC>
+cudaError_t psi_dispatch(const KParams &P, const void *g, void *psi, unsigned *err, const Launch &L) {
+  using S = typename Types<PREC>::S;
+  using Psi = typename Types<PREC>::Psi;
+  const dim3 grid = node_grid(P, L), block(L.bx, L.by);
+  switch (P.eos) {
+    case kEosCS:
+      psi_kernel<PREC, kEosCS><<<grid, block, 0, L.stream>>>((const S *)g, (Psi *)psi, P, err);
+      break;
+    case kEosExp:
+      psi_kernel<PREC, kEosExp><<<grid, block, 0, L.stream>>>((const S *)g, (Psi *)psi, P, err);
+      break;
+    default:
+      psi_kernel<PREC, kEosNone><<<grid, block, 0, L.stream>>>((const S *)g, (Psi *)psi, P, err);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+template <int PREC, int OP>
+cudaError_t fused_dispatch(const KParams &P, bool sigma, const void *g_in, void *g_out, const void *psi,
+                           const Launch &L) {
+  using S = typename Types<PREC>::S;
+  using Psi = typename Types<PREC>::Psi;
+  const dim3 grid = node_grid(P, L), block(L.bx, L.by);
+  if (sigma)
+    fused_kernel<PREC, OP, true><<<grid, block, 0, L.stream>>>((const S *)g_in, (S *)g_out, (const Psi *)psi, P);
+  else
+    fused_kernel<PREC, OP, false><<<grid, block, 0, L.stream>>>((const S *)g_in, (S *)g_out, (const Psi *)psi, P);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_psi(const KParams &P, int precision, const void *g, void *psi, unsigned *err,
+                       const Launch &L) {
+  switch (precision) {
+    case kF64: return psi_dispatch<kF64>(P, g, psi, err, L);
+    case kF32: return psi_dispatch<kF32>(P, g, psi, err, L);
+    default: return psi_dispatch<kF16>(P, g, psi, err, L);
+  }
+}
+
+cudaError_t launch_fused(const KParams &P, int precision, int op, bool sigma, const void *g_in, void *g_out,
+                         const void *psi, const Launch &L) {
+  if (op == kNonOrth) {
+    switch (precision) {
+      case kF64: return fused_dispatch<kF64, kNonOrth>(P, sigma, g_in, g_out, psi, L);
+      case kF32: return fused_dispatch<kF32, kNonOrth>(P, sigma, g_in, g_out, psi, L);
+      default: return fused_dispatch<kF16, kNonOrth>(P, sigma, g_in, g_out, psi, L);
+    }
+  }
+  switch (precision) {
+    case kF64: return fused_dispatch<kF64, kOrth>(P, sigma, g_in, g_out, psi, L);
+    case kF32: return fused_dispatch<kF32, kOrth>(P, sigma, g_in, g_out, psi, L);
+    default: return fused_dispatch<kF16, kOrth>(P, sigma, g_in, g_out, psi, L);
+  }
+}
+
+#define LBM_PREC_SWITCH(precision, CALL) \
+  switch (precision) {                   \
+    case kF64: { constexpr int PR = kF64; CALL; } break; \
+    case kF32: { constexpr int PR = kF32; CALL; } break; \
+    default: { constexpr int PR = kF16; CALL; } break;   \
+  }
+
+cudaError_t launch_moments(const KParams &P, int precision, const void *g, const void *psi, double *rho,
+                           double *u, const Launch &L) {
+  const dim3 grid = node_grid(P, L), block(L.bx, L.by);
+  LBM_PREC_SWITCH(precision, (moments_kernel<PR><<<grid, block, 0, L.stream>>>(
+                                 (const typename Types<PR>::S *)g, (const typename Types<PR>::Psi *)psi, P, rho, u)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag(const KParams &P, int precision, const void *g, const void *psi, double *partials,
+                        double *result, const Launch &L) {
+  LBM_PREC_SWITCH(precision, (diag_partial_kernel<PR><<<kReduceBlocks, 256, 0, L.stream>>>(
+                                 (const typename Types<PR>::S *)g, (const typename Types<PR>::Psi *)psi, P, partials)));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  diag_final_kernel<<<1, 32, 0, L.stream>>>(partials, kReduceBlocks, result);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho_droplets(const KParams &P, double *rho, const DropletChunk &chunk, double W,
+                                double rho_l, double rho_v, bool first, const Launch &L) {
+  rho_droplets_kernel<<<node_grid(P, L), dim3(L.bx, L.by), 0, L.stream>>>(rho, P, chunk, W, rho_l, rho_v,
+                                                                           first ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rho_slab(const KParams &P, double *rho, int axis, double lo, double hi, double W,
+                            double rho_l, double rho_v, const Launch &L) {
+  rho_slab_kernel<<<node_grid(P, L), dim3(L.bx, L.by), 0, L.stream>>>(rho, P, axis, lo, hi, W, rho_l, rho_v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_state_from_rho(const KParams &P, int precision, const double *rho, void *g, const Launch &L) {
+  const dim3 grid = node_grid(P, L), block(L.bx, L.by);
+  LBM_PREC_SWITCH(precision, (state_from_rho_kernel<PR><<<grid, block, 0, L.stream>>>(
+                                 rho, (typename Types<PR>::S *)g, P)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_populations(const KParams &P, int precision, const void *g, double *out, int a_lo,
+                                   int a_hi, const Launch &L) {
+  const dim3 grid = node_grid(P, L), block(L.bx, L.by);
+  LBM_PREC_SWITCH(precision, (get_populations_kernel<PR><<<grid, block, 0, L.stream>>>(
+                                 (const typename Types<PR>::S *)g, out, P, a_lo, a_hi)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_populations(const KParams &P, int precision, const double *f, void *g, int a_lo,
+                                   int a_hi, const Launch &L) {
+  const dim3 grid = node_grid(P, L), block(L.bx, L.by);
+  LBM_PREC_SWITCH(precision, (set_populations_kernel<PR><<<grid, block, 0, L.stream>>>(
+                                 f, (typename Types<PR>::S *)g, P, a_lo, a_hi)));
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,247 @@
+"""ctypes binding of the C ABI in include/lbm.h (argument marshalling only).
+
+Every numerical step runs in liblbm.so's CUDA kernels.  PyTorch provides the
+device memory (``lbm_bind``) and the stream (the current torch stream).  If
+the library is missing this module raises at import: there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_EOS_DOMAIN, ERR_TIMEOUT, ERR_STATE = range(8)
+OPERATORS = {"orth": 0, "nonorth": 1}
+PRECISIONS = {"f64": 0, "f32": 1, "f16": 2}
+EOS_KINDS = {"cs": 0, "exp": 1, "none": 2}
+
+# Every symbol include/lbm.h declares, with (restype, argtypes).
+_c_int, _c_double, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_szp = ctypes.POINTER(ctypes.c_size_t)
+_llp = ctypes.POINTER(ctypes.c_longlong)
+
+
+class LbmEos(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("a", _c_double), ("b", _c_double), ("R", _c_double),
+                ("T", _c_double), ("psi0", _c_double), ("rho0", _c_double)]
+
+
+class LbmRates(ctypes.Structure):
+    _fields_ = [("s_e", _c_double), ("s_nu", _c_double), ("s_q", _c_double), ("s_pi", _c_double),
+                ("s_eps", _c_double), ("s_m", _c_double)]
+
+
+SIGNATURES = {
+    "lbm_create": (_c_int, [ctypes.POINTER(ctypes.c_int * 3), ctypes.POINTER(LbmEos), _c_double,
+                            ctypes.POINTER(LbmRates), _c_int, _c_int, _c_double, _vp,
+                            ctypes.POINTER(_vp)]),
+    "lbm_buffer_bytes": (_c_int, [_vp, _szp, _szp, _szp]),
+    "lbm_bind": (_c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "lbm_init_droplet": (_c_int, [_vp, _dp, _c_double, _c_double, _c_double, _c_double]),
+    "lbm_init_droplets": (_c_int, [_vp, _c_int, _dp, _dp, _c_double, _c_double, _c_double]),
+    "lbm_init_flat": (_c_int, [_vp, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double]),
+    "lbm_init_field": (_c_int, [_vp, _vp, _c_int, _c_double]),
+    "lbm_step": (_c_int, [_vp, _c_int]),
+    "lbm_moments": (_c_int, [_vp, _vp, _vp, _c_int]),
+    "lbm_get_populations": (_c_int, [_vp, _vp, _c_int]),
+    "lbm_set_populations": (_c_int, [_vp, _vp, _c_int]),
+    "lbm_diag": (_c_int, [_vp, _dp]),
+    "lbm_check": (_c_int, [_vp]),
+    "lbm_set_check_interval": (_c_int, [_vp, _c_int]),
+    "lbm_set_profiling": (_c_int, [_vp, _c_int]),
+    "lbm_kernel_times": (_c_int, [_vp, _dp, _llp, _dp, _llp]),
+    "lbm_step_count": (ctypes.c_longlong, [_vp]),
+    "lbm_destroy": (None, [_vp]),
+    "lbm_last_error": (ctypes.c_char_p, [_vp]),
+    "lbm_status_string": (ctypes.c_char_p, [_c_int]),
+}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1805_08643_gb300._build.build() "
+                          "(the CUDA path has no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = load_library()
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        name = lib.lbm_status_string(status).decode()
+        super().__init__(f"{where}: {name}" + (f" ({detail})" if detail else ""))
+
+
+@dataclass
+class Rates:
+    """Relaxation rates (see lbm_rates in include/lbm.h)."""
+
+    s_e: float = 1.1
+    s_nu: float = 1.0
+    s_q: float = 1.1
+    s_pi: float = 1.1
+    s_eps: float = 1.1
+    s_m: float = 1.1
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Lattice:
+    """One periodic D3Q19 box on the current CUDA device.
+
+    Device buffers come from PyTorch and are bound to the C context; work runs
+    on the current torch stream (or ``stream``, a torch.cuda.Stream).
+    """
+
+    def __init__(self, grid, operator="nonorth", precision="f64", eos="cs", a=1.0, b=4.0, R=1.0,
+                 T=0.0, psi0=1.0, rho0=1.0, G=-1.0, rates: Rates | None = None, sigma=0.0,
+                 stream=None, torch_buffers=True):
+        import torch
+
+        self.grid = tuple(int(v) for v in grid)
+        self.n = self.grid[0] * self.grid[1] * self.grid[2]
+        self.operator, self.precision = operator, precision
+        rates = rates or Rates()
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        eos_s = LbmEos(EOS_KINDS[eos], a, b, R, T, psi0, rho0)
+        rates_s = LbmRates(rates.s_e, rates.s_nu, rates.s_q, rates.s_pi, rates.s_eps, rates.s_m)
+        g = (ctypes.c_int * 3)(*self.grid)
+        handle = ctypes.c_void_p()
+        st = lib.lbm_create(ctypes.byref(g), ctypes.byref(eos_s), G, ctypes.byref(rates_s),
+                            OPERATORS[operator], PRECISIONS[precision], sigma,
+                            ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(handle))
+        if st != OK:
+            raise LBMError(st, "lbm_create")
+        self._h = handle
+        self._buffers = []
+        if torch_buffers:
+            pb, sb, xb = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+            self._check(lib.lbm_buffer_bytes(self._h, ctypes.byref(pb), ctypes.byref(sb),
+                                             ctypes.byref(xb)), "lbm_buffer_bytes")
+            dev = torch.device("cuda", torch.cuda.current_device())
+            self._buffers = [torch.empty(int(v), dtype=torch.uint8, device=dev)
+                             for v in (pb.value, pb.value, sb.value, xb.value)]
+            self._check(lib.lbm_bind(self._h, *[ctypes.c_void_p(t.data_ptr()) for t in self._buffers]),
+                        "lbm_bind")
+
+    # -------------------------------------------------------------- plumbing
+    def _check(self, status, where):
+        if status != OK:
+            raise LBMError(status, where, lib.lbm_last_error(self._h).decode())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.lbm_destroy(self._h)
+            self._h = None
+            self._buffers = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -------------------------------------------------------------- state
+    def init_droplet(self, centre, R, W, rho_l, rho_v):
+        c = (ctypes.c_double * 3)(*centre)
+        self._check(lib.lbm_init_droplet(self._h, c, R, W, rho_l, rho_v), "lbm_init_droplet")
+
+    def init_droplets(self, centres, radii, W, rho_l, rho_v):
+        c = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+        r = np.ascontiguousarray(radii, dtype=np.float64).reshape(-1)
+        self._check(lib.lbm_init_droplets(self._h, len(r), c.ctypes.data_as(_dp), r.ctypes.data_as(_dp),
+                                          W, rho_l, rho_v), "lbm_init_droplets")
+
+    def init_flat(self, axis, lo, hi, W, rho_l, rho_v):
+        self._check(lib.lbm_init_flat(self._h, axis, lo, hi, W, rho_l, rho_v), "lbm_init_flat")
+
+    def init_field(self, rho, rho_ref):
+        """rho: numpy array (host) or CUDA torch tensor of N float64, x fastest."""
+        if isinstance(rho, np.ndarray):
+            a = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+            assert a.size == self.n
+            self._check(lib.lbm_init_field(self._h, _ptr(a), 0, rho_ref), "lbm_init_field")
+        else:
+            assert rho.is_cuda and rho.dtype.is_floating_point and rho.numel() == self.n
+            t = rho.contiguous().double()
+            self._check(lib.lbm_init_field(self._h, ctypes.c_void_p(t.data_ptr()), 1, rho_ref),
+                        "lbm_init_field")
+
+    def step(self, n=1):
+        self._check(lib.lbm_step(self._h, int(n)), "lbm_step")
+
+    @property
+    def steps(self):
+        return lib.lbm_step_count(self._h)
+
+    def moments(self):
+        """(rho, u) as float64 numpy arrays of shapes (Nz,Ny,Nx) and (3,Nz,Ny,Nx)."""
+        nx, ny, nz = self.grid
+        rho = np.empty(self.n)
+        u = np.empty(3 * self.n)
+        self._check(lib.lbm_moments(self._h, _ptr(rho), _ptr(u), 0), "lbm_moments")
+        return rho.reshape(nz, ny, nx), u.reshape(3, nz, ny, nx)
+
+    def moments_device(self, rho_t, u_t):
+        """Write rho (N) and u (3N) into CUDA float64 tensors."""
+        self._check(lib.lbm_moments(self._h, ctypes.c_void_p(rho_t.data_ptr()),
+                                    ctypes.c_void_p(u_t.data_ptr()), 1), "lbm_moments")
+
+    def populations(self):
+        nx, ny, nz = self.grid
+        f = np.empty(19 * self.n)
+        self._check(lib.lbm_get_populations(self._h, _ptr(f), 0), "lbm_get_populations")
+        return f.reshape(19, nz, ny, nx)
+
+    def set_populations(self, f):
+        a = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
+        assert a.size == 19 * self.n
+        self._check(lib.lbm_set_populations(self._h, _ptr(a), 0), "lbm_set_populations")
+
+    def diag(self):
+        out = (ctypes.c_double * 5)()
+        self._check(lib.lbm_diag(self._h, out), "lbm_diag")
+        return {"mass": out[0], "momentum": (out[1], out[2], out[3]), "max_u": out[4]}
+
+    def check(self):
+        return lib.lbm_check(self._h)
+
+    def set_check_interval(self, k):
+        self._check(lib.lbm_set_check_interval(self._h, int(k)), "lbm_set_check_interval")
+
+    def set_profiling(self, on=True):
+        self._check(lib.lbm_set_profiling(self._h, 1 if on else 0), "lbm_set_profiling")
+
+    def kernel_times(self):
+        mp, mf = ctypes.c_double(), ctypes.c_double()
+        npsi, nf = ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(lib.lbm_kernel_times(self._h, ctypes.byref(mp), ctypes.byref(npsi), ctypes.byref(mf),
+                                         ctypes.byref(nf)), "lbm_kernel_times")
+        return {"psi_ms": mp.value, "psi_launches": npsi.value, "fused_ms": mf.value,
+                "fused_launches": nf.value}

@@ -1,0 +1,75 @@
+"""The C ABI library loads and exports what include/lbm.h declares (no GPU needed)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_1805_08643_gb300 import _build
+
+    _build.build()
+    from paper_1805_08643_gb300 import lbm as mod
+
+    return mod
+
+
+def test_header_declares_the_boundary():
+    syms = _declared_symbols()
+    for name in ("lbm_create", "lbm_init_droplet", "lbm_init_flat", "lbm_step", "lbm_moments",
+                 "lbm_destroy", "lbm_last_error"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(lbm):
+    lib = ctypes.CDLL(lbm.LIB_PATH)
+    for name in _declared_symbols():
+        assert hasattr(lib, name), name
+    assert set(_declared_symbols()) == set(lbm.SIGNATURES)
+
+
+def _create(lbm, grid=(8, 8, 8), op=1, prec=0, eos_kind=0, G=-1.0, sigma=0.0, rates=None):
+    eos = lbm.LbmEos(eos_kind, 1.0, 4.0, 1.0, 0.07, 1.0, 1.0)
+    r = lbm.LbmRates(*(rates or (1.1, 1.0, 1.1, 1.1, 1.1, 1.1)))
+    g = (ctypes.c_int * 3)(*grid)
+    h = ctypes.c_void_p()
+    st = lbm.lib.lbm_create(ctypes.byref(g), ctypes.byref(eos), G, ctypes.byref(r), op, prec, sigma,
+                            None, ctypes.byref(h))
+    return st, h
+
+
+def test_create_validates_arguments_without_touching_the_gpu(lbm):
+    assert _create(lbm, grid=(2, 8, 8))[0] == lbm.ERR_ARG
+    assert _create(lbm, op=5)[0] == lbm.ERR_ARG
+    assert _create(lbm, prec=3)[0] == lbm.ERR_ARG
+    assert _create(lbm, eos_kind=7)[0] == lbm.ERR_ARG
+    assert _create(lbm, rates=(2.5, 1, 1, 1, 1, 1))[0] == lbm.ERR_ARG
+    assert _create(lbm, G=0.0)[0] == lbm.ERR_ARG  # sqrt pseudopotential needs G != 0
+    assert _create(lbm, eos_kind=2, sigma=0.1)[0] == lbm.ERR_ARG
+    st, h = _create(lbm)
+    assert st == lbm.OK and h.value
+    # state errors are caught on the host before any launch
+    assert lbm.lib.lbm_step(h, 1) == lbm.ERR_STATE
+    assert b"before an init" in lbm.lib.lbm_last_error(h)
+    assert lbm.lib.lbm_step(h, 0) == lbm.ERR_ARG
+    assert lbm.lib.lbm_step_count(h) == 0
+    pb, sb, xb = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    assert lbm.lib.lbm_buffer_bytes(h, ctypes.byref(pb), ctypes.byref(sb), ctypes.byref(xb)) == lbm.OK
+    assert pb.value == 19 * 512 * 8 and sb.value == 512 * 8
+    lbm.lib.lbm_destroy(h)
+    st, h = _create(lbm, prec=2)
+    lbm.lib.lbm_buffer_bytes(h, ctypes.byref(pb), ctypes.byref(sb), ctypes.byref(xb))
+    assert pb.value == 19 * 512 * 2 and sb.value == 512 * 4
+    lbm.lib.lbm_destroy(h)
+    assert lbm.lib.lbm_status_string(4) == b"LBM_ERR_NONFINITE"
