@@ -160,6 +160,29 @@ lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
 /* Steps taken since the last init or lbm_set_populations. */
 long long lbm_step_count(const lbm_ctx *ctx);
 
+/* One FP64 time step that allocates no device memory (the paper has no
+ * counterpart; this is a library service).  For callers that cannot call
+ * cudaMalloc: code running while a CUDA graph is captured, hosts whose device
+ * memory belongs to another allocator, loops that must never allocate.
+ *  - f_in: the post-streaming populations f_a(x, t) of the box, device memory,
+ *    19N doubles in the public SoA layout (as lbm_get_populations returns them);
+ *    f_out (distinct, same layout) receives f_a(x, t + 1).  The caller owns both.
+ *  - ctx supplies the box, physics and stream only; it must be LBM_F64.  Its own
+ *    populations and buffers are neither read nor written, and it need not be
+ *    initialised or bound.
+ *  - The psi scratch is a static device array of 2^21 doubles (16 MiB, boxes of
+ *    up to 2^21 nodes, e.g. 128^3) that every GPU loading the library holds until
+ *    exit; larger boxes return LBM_ERR_ARG.  All calls share it: calls whose work
+ *    overlaps on the GPU (different streams, or other processes' contexts in
+ *    flight at once on one device) race and give wrong results.  Each call
+ *    rewrites all psi it reads, so nothing needs clearing between calls.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Asynchronous on the context's stream.  A density outside the EOS domain
+ *    gives NaN populations in f_out (there is no error word on this path).
+ * Errors: LBM_ERR_ARG (null or aliased pointers, precision, size), LBM_ERR_CUDA. */
+lbm_status lbm_step_static(const lbm_ctx *ctx, const double *f_in, double *f_out);
+
 /* Release the context and any device memory it allocated itself. */
 void lbm_destroy(lbm_ctx *ctx);
 

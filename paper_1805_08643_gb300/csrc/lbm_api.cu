@@ -437,3 +437,16 @@ void lbm_destroy(lbm_ctx *c) {
 }
 
 }  // extern "C"
+
+// Read-only view of a context's parameters for other translation units.
+namespace lbm {
+bool ctx_params(const lbm_ctx *c, KParams *P, int *precision, int *op, bool *sigma_on, cudaStream_t *stream) {
+  if (!c) return false;
+  *P = c->P;
+  *precision = c->precision;
+  *op = c->op;
+  *sigma_on = c->sigma_on;
+  *stream = c->L.stream;
+  return true;
+}
+}  // namespace lbm

@@ -58,6 +58,7 @@ SIGNATURES = {
     "lbm_set_profiling": (_c_int, [_vp, _c_int]),
     "lbm_kernel_times": (_c_int, [_vp, _dp, _llp, _dp, _llp]),
     "lbm_step_count": (ctypes.c_longlong, [_vp]),
+    "lbm_step_static": (_c_int, [_vp, _vp, _vp]),
     "lbm_destroy": (None, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
     "lbm_status_string": (ctypes.c_char_p, [_c_int]),
