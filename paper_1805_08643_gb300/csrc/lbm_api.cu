@@ -189,6 +189,20 @@ lbm_status lbm_create(const int grid[3], const lbm_eos *eos, double G, const lbm
   P.RT = eos->R * eos->T;
   P.psi0 = eos->psi0;
   P.rho0 = eos->rho0;
+  P.b4 = 0.25 * eos->b;
+  P.two_over_G = P.G != 0.0 ? 2.0 / P.G : 0.0;
+  {
+    // coefficients of the radicand polynomial (see KParams)
+    const double cc = P.b4, rt = P.RT, aa = P.a, k = P.two_over_G;
+    P.q0 = k * (rt - 1.0 / 3.0);
+    P.q1 = k * (rt * cc - aa + cc);
+    P.q2 = k * (rt * cc * cc + 3.0 * aa * cc - cc * cc);
+    P.q3 = k * (-rt * cc * cc * cc - 3.0 * aa * cc * cc + cc * cc * cc / 3.0);
+    P.q4 = k * (aa * cc * cc * cc);
+    P.f_rho_max = eos->b > 0 ? (float)(4.0 / eos->b) : 0.0f;
+  }
+  lbm::refresh_float_params(P);
+  lbm::refresh_float_params(P);
   c->precision = precision;
   c->op = op;
   c->sigma_on = sigma != 0.0;
@@ -235,6 +249,7 @@ lbm_status lbm_init_droplets(lbm_ctx *c, int n, const double *centres, const dou
   lbm_status s = ensure_buffers(c);
   if (s != LBM_OK) return s;
   c->P.rho_ref = rho_v;
+  lbm::refresh_float_params(c->P);
   double *rho = (double *)spare(c);
   for (int k0 = 0; k0 < n; k0 += lbm::kDropletChunk) {
     lbm::DropletChunk ch{};
@@ -264,6 +279,7 @@ lbm_status lbm_init_flat(lbm_ctx *c, int axis, double lo, double hi, double W, d
   lbm_status s = ensure_buffers(c);
   if (s != LBM_OK) return s;
   c->P.rho_ref = rho_v;
+  lbm::refresh_float_params(c->P);
   double *rho = (double *)spare(c);
   CK(lbm::launch_rho_slab(c->P, rho, axis, lo, hi, W, rho_l, rho_v, c->L), "rho_slab kernel");
   return finish_init(c, rho);
@@ -274,6 +290,7 @@ lbm_status lbm_init_field(lbm_ctx *c, const double *rho, int on_device, double r
   lbm_status s = ensure_buffers(c);
   if (s != LBM_OK) return s;
   c->P.rho_ref = rho_ref;
+  lbm::refresh_float_params(c->P);
   const double *src = rho;
   if (!on_device) {
     double *tmp = (double *)spare(c);

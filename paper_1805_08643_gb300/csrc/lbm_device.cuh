@@ -116,22 +116,35 @@ __device__ __forceinline__ void pull(const S *__restrict__ g, int n, const Nbhd 
 // ------------------------------------------------------------------ EOS
 // psi(rho): square-root form sqrt(2 (p_EOS - rho/3) / G) with the
 // Carnahan-Starling p_EOS of Eq. 58, or psi0 exp(-rho0/rho) (Sec. II B).
+// With eta = b rho/4, num = 1 + eta + eta^2 - eta^3 and den = (1 - eta)^3 the
+// radicand is X / den, X = (2/G) rho (RT num - (a rho + 1/3) den): a quintic in
+// rho with no division, evaluated by Horner's rule from host-made coefficients
+// (KParams::q0..q4), always in FP64 (the repulsive and attractive parts of
+// p_EOS cancel there).  psi = X rsqrt(X den); the FP32-psi forms take den and
+// the root in FP32, the precision psi is stored in.
 // Outside the domain (rho <= 0 or not finite, b rho/4 >= 1, negative radicand)
 // it flags the error and returns NaN: the state is never clamped.
-template <int EOS>
-__device__ __forceinline__ double eos_psi(double rho, const KParams &P, unsigned &err) {
-  if (EOS == kEosNone) return 0.0;
-  if (!isfinite(rho)) { err |= kErrNonFinite; return __longlong_as_double(0x7ff8000000000000LL); }
-  if (!(rho > 0.0)) { err |= kErrEosDomain; return __longlong_as_double(0x7ff8000000000000LL); }
-  if (EOS == kEosExp) return P.psi0 * exp(-P.rho0 / rho);
-  const double eta = 0.25 * P.b * rho;
-  if (!(eta < 1.0)) { err |= kErrEosDomain; return __longlong_as_double(0x7ff8000000000000LL); }
-  const double one_m = 1.0 - eta;
-  const double num = 1.0 + eta * (1.0 + eta * (1.0 - eta));
-  const double p = rho * P.RT * num / (one_m * one_m * one_m) - P.a * rho * rho;
-  const double rad = 2.0 * (p - rho * (1.0 / 3.0)) / P.G;
-  if (!(rad >= 0.0)) { err |= kErrEosDomain; return __longlong_as_double(0x7ff8000000000000LL); }
-  return sqrt(rad);
+// rho_f is rho rounded to FP32 (used for the domain checks and the final root).
+template <int EOS, typename PsiT>
+__device__ __forceinline__ PsiT eos_psi(double rho, float rho_f, const KParams &P, unsigned &err) {
+  const PsiT nan = (PsiT)__longlong_as_double(0x7ff8000000000000LL);
+  if (EOS == kEosNone) return PsiT(0);
+  if (!isfinite(rho_f)) { err |= kErrNonFinite; return nan; }
+  if (!(rho_f > 0.0f)) { err |= kErrEosDomain; return nan; }
+  if (EOS == kEosExp) return (PsiT)(P.psi0 * exp(-P.rho0 / rho));
+  if (!(rho_f < P.f_rho_max)) { err |= kErrEosDomain; return nan; }
+  const double X = rho * fma(fma(fma(fma(P.q4, rho, P.q3), rho, P.q2), rho, P.q1), rho, P.q0);
+  if (sizeof(PsiT) == sizeof(double)) {
+    if (!(X >= 0.0)) { err |= kErrEosDomain; return nan; }
+    if (X == 0.0) return PsiT(0);
+    const double one_m = fma(-P.b4, rho, 1.0);
+    return (PsiT)(X * rsqrt(X * (one_m * one_m * one_m)));
+  }
+  const float xf = (float)X;
+  if (!(xf >= 0.0f)) { err |= kErrEosDomain; return nan; }
+  if (xf == 0.0f) return PsiT(0);
+  const float one_m = fmaf(-P.fb4, rho_f, 1.0f);
+  return (PsiT)(xf * rsqrtf(xf * (one_m * one_m * one_m)));
 }
 
 // ------------------------------------------------------------------ force
@@ -148,10 +161,29 @@ __device__ __forceinline__ void psi_gradient(const T p[19], T &Sx, T &Sy, T &Sz)
 }
 
 // ------------------------------------------------------------------ collision
-template <typename T> struct Rates {
-  T se, snu, sq, spi, seps, sm;
+template <typename T> struct Rates;
+template <> struct Rates<double> {
+  double se, snu, sq, spi, seps, sm;
   __device__ __forceinline__ explicit Rates(const KParams &P)
-      : se((T)P.s_e), snu((T)P.s_nu), sq((T)P.s_q), spi((T)P.s_pi), seps((T)P.s_eps), sm((T)P.s_m) {}
+      : se(P.s_e), snu(P.s_nu), sq(P.s_q), spi(P.s_pi), seps(P.s_eps), sm(P.s_m) {}
+};
+template <> struct Rates<float> {
+  float se, snu, sq, spi, seps, sm;
+  __device__ __forceinline__ explicit Rates(const KParams &P)
+      : se(P.fs_e), snu(P.fs_nu), sq(P.fs_q), spi(P.fs_pi), seps(P.fs_eps), sm(P.fs_m) {}
+};
+
+// Parameters in the arithmetic type of a kernel (FP32 kernels read the float copies).
+template <typename T> struct Phys;
+template <> struct Phys<double> {
+  static __device__ __forceinline__ double G(const KParams &P) { return P.G; }
+  static __device__ __forceinline__ double rho_ref(const KParams &P) { return P.rho_ref; }
+  static __device__ __forceinline__ double sigma_coef(const KParams &P) { return P.sigma_coef; }
+};
+template <> struct Phys<float> {
+  static __device__ __forceinline__ float G(const KParams &P) { return P.fG; }
+  static __device__ __forceinline__ float rho_ref(const KParams &P) { return P.frho_ref; }
+  static __device__ __forceinline__ float sigma_coef(const KParams &P) { return P.fsigma_coef; }
 };
 
 // relax one moment: m* = m - s (m - m_eq) + (1 - s/2) S   (Eq. 4)

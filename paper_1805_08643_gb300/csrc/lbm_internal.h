@@ -29,6 +29,14 @@ struct KParams {
   int eos;
   double a, b, RT;   // Carnahan-Starling (Eq. 58), RT = R * T
   double psi0, rho0; // exponential pseudopotential
+  double b4;         // b / 4
+  double two_over_G; // 2 / G
+  // (2/G) (RT num - (a rho + 1/3) den) = q0 + q1 rho + q2 rho^2 + q3 rho^3 + q4 rho^4,
+  // num = 1 + eta + eta^2 - eta^3, den = (1 - eta)^3, eta = b rho / 4 (Eq. 58)
+  double q0, q1, q2, q3, q4;
+  float f_rho_max;   // 4 / b: the packing limit eta < 1
+  // FP32 copies for the reduced-precision kernels (no conversions on device)
+  float fG, frho_ref, fs_e, fs_nu, fs_q, fs_pi, fs_eps, fs_m, fsigma_coef, fb4;
 };
 
 // Layout of the scratch buffer.
@@ -49,6 +57,20 @@ struct Launch {
   cudaStream_t stream;
   int bx, by;  // thread-block shape (x, y) of the per-node kernels
 };
+
+// Fill the FP32 copies of KParams from its doubles (call after any change).
+inline void refresh_float_params(KParams &P) {
+  P.fG = (float)P.G;
+  P.frho_ref = (float)P.rho_ref;
+  P.fs_e = (float)P.s_e;
+  P.fs_nu = (float)P.s_nu;
+  P.fs_q = (float)P.s_q;
+  P.fs_pi = (float)P.s_pi;
+  P.fs_eps = (float)P.s_eps;
+  P.fs_m = (float)P.s_m;
+  P.fsigma_coef = (float)P.sigma_coef;
+  P.fb4 = (float)P.b4;
+}
 
 size_t storage_bytes(int precision);  // bytes per stored population
 size_t psi_elem_bytes(int precision);

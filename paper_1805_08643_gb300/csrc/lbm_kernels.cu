@@ -51,8 +51,9 @@ __global__ void __launch_bounds__(256) psi_kernel(const typename Types<PREC>::S 
                 ((f[15] + f[16]) + (f[17] + f[18]));
   const T drho = f[0] + sax + sdg;
   unsigned e = 0;
-  const double v = eos_psi<EOS>(P.rho_ref + (double)drho, P, e);
-  psi[nb.self] = (typename Types<PREC>::Psi)v;
+  const double rho = P.rho_ref + (double)drho;
+  const float rho_f = sizeof(T) == sizeof(double) ? (float)rho : Phys<T>::rho_ref(P) + (float)drho;
+  psi[nb.self] = eos_psi<EOS, typename Types<PREC>::Psi>(rho, rho_f, P, e);
   if (e) atomicOr(err, e);
 }
 
@@ -76,15 +77,15 @@ __global__ void __launch_bounds__(256) fused_kernel(const typename Types<PREC>::
   p[0] = (T)__ldg(psi + nb.self);
   T Sx, Sy, Sz;
   psi_gradient<T>(p, Sx, Sy, Sz);
-  const T mG = (T)(-P.G);
-  const T Fx = mG * p[0] * Sx, Fy = mG * p[0] * Sy, Fz = mG * p[0] * Sz;
+  const T k = -Phys<T>::G(P) * p[0];
+  const T Fx = k * Sx, Fy = k * Sy, Fz = k * Sz;
   // Eq. 16: 6 sigma |F|^2 / (psi^2 (1/s_e - 1/2)) = sigma_coef |S|^2
-  const T dS4 = SIGMA ? (T)P.sigma_coef * (Sx * Sx + Sy * Sy + Sz * Sz) : T(0);
+  const T dS4 = SIGMA ? Phys<T>::sigma_coef(P) * (Sx * Sx + Sy * Sy + Sz * Sz) : T(0);
   const Rates<T> r(P);
   if (OP == kNonOrth)
-    collide_nonorth<T>(f, (T)P.rho_ref, Fx, Fy, Fz, dS4, r);
+    collide_nonorth<T>(f, Phys<T>::rho_ref(P), Fx, Fy, Fz, dS4, r);
   else
-    collide_orth<T>(f, (T)P.rho_ref, Fx, Fy, Fz, dS4, r);
+    collide_orth<T>(f, Phys<T>::rho_ref(P), Fx, Fy, Fz, dS4, r);
 #pragma unroll
   for (int a = 0; a < 19; ++a) Storage<S>::store(g_out + (size_t)a * P.n + nb.self, a, f[a]);
 }

@@ -38,7 +38,7 @@ __global__ void static_psi_kernel(const double *__restrict__ f, double *__restri
 #pragma unroll
   for (int a = 0; a < 19; ++a) rho += f[(size_t)a * P.n + i];
   unsigned e = 0;
-  psi[i] = lbm::eos_psi<EOS>(rho, P, e);  // out of the EOS domain: NaN, which reaches f_out
+  psi[i] = lbm::eos_psi<EOS, double>(rho, (float)rho, P, e);  // out of the EOS domain: NaN, which reaches f_out
 }
 
 // Collide f_a(x, t) and push f*_a(x, t) to f_out at x + e_a (Eq. 5).
