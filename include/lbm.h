@@ -92,8 +92,8 @@ lbm_status lbm_create(const int grid[3], const lbm_eos *eos, double G,
                       void *cuda_stream, lbm_ctx **out);
 
 /* Bytes of the three device buffers a context needs: each of the two
- * population buffers, the psi buffer, and the scratch buffer (reductions and
- * the error word). */
+ * population buffers, the psi buffer (two time levels of psi), and the scratch
+ * buffer (reductions and the error word). */
 lbm_status lbm_buffer_bytes(const lbm_ctx *ctx, size_t *population_bytes,
                             size_t *psi_bytes, size_t *scratch_bytes);
 
@@ -156,6 +156,15 @@ lbm_status lbm_set_check_interval(lbm_ctx *ctx, int k);
 lbm_status lbm_set_profiling(lbm_ctx *ctx, int enabled);
 lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
                             double *ms_fused, long long *n_fused);
+
+/* Kernel choice for this context.  single_pass = 1 (LBM_F32 and
+ * LBM_F32_STORE_F16 only) runs each step as one kernel that also produces psi
+ * of the next step, recomputing collisions on a one-node ring around each
+ * thread block's tile; 0 (the default) runs the psi pass and the fused pass.  tile picks the x-y tile of the single-pass kernel (0: 32x4, 1: 32x8,
+ * 2: 64x4); z_planes the z planes each thread block marches through (0 =
+ * automatic).  Results do not depend on tile or z_planes.  Errors: LBM_ERR_ARG. */
+lbm_status lbm_set_tuning(lbm_ctx *ctx, int single_pass, int tile, int z_planes);
+lbm_status lbm_get_tuning(const lbm_ctx *ctx, int *single_pass, int *tile, int *z_planes);
 
 /* Steps taken since the last init or lbm_set_populations. */
 long long lbm_step_count(const lbm_ctx *ctx);

@@ -22,8 +22,11 @@ struct lbm_ctx {
   lbm::Launch L{};
   void *g[2] = {nullptr, nullptr};
   int cur = 0;
-  void *psi = nullptr;
+  void *psi = nullptr;      // two time levels of psi, each N elements
+  int pc = 0;               // which level holds psi of the current state
   void *scratch = nullptr;
+  bool onepass = false;     // single-pass kernel (FP32 arithmetic forms)
+  int tile = 1, zc = 0;     // its tile shape and z planes per CTA (0 = automatic)
   bool owns = false, have_buffers = false, initialized = false, psi_valid = false;
   long long steps = 0;
   int check_interval = 0;
@@ -55,7 +58,23 @@ lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *where) {
   } while (0)
 
 size_t pop_bytes(const lbm_ctx *c) { return (size_t)19 * c->P.n * lbm::storage_bytes(c->precision); }
-size_t psi_bytes(const lbm_ctx *c) { return (size_t)c->P.n * lbm::psi_elem_bytes(c->precision); }
+size_t psi_bytes(const lbm_ctx *c) { return 2 * (size_t)c->P.n * lbm::psi_elem_bytes(c->precision); }
+void *psi_at(lbm_ctx *c, int level) {
+  return (char *)c->psi + (size_t)level * c->P.n * lbm::psi_elem_bytes(c->precision);
+}
+void *cur_psi(lbm_ctx *c) { return psi_at(c, c->pc); }
+
+// z planes per CTA of the single-pass kernel: about eight CTAs per SM in total,
+// at least 8 planes so that the two recomputed boundary planes stay cheap.
+int auto_zc(const lbm_ctx *c) {
+  const int bx = c->tile == lbm::kTile64x4 ? 64 : 32, by = c->tile == lbm::kTile32x8 ? 8 : 4;
+  const long long tiles = (long long)((c->P.nx + bx - 1) / bx) * ((c->P.ny + by - 1) / by);
+  long long chunks = (8LL * 152 + tiles / 2) / tiles;
+  if (chunks < 1) chunks = 1;
+  int zc = (int)((c->P.nz + chunks - 1) / chunks);
+  if (zc < 8) zc = 8;
+  return zc > c->P.nz ? c->P.nz : zc;
+}
 
 unsigned *err_word(lbm_ctx *c) { return (unsigned *)((char *)c->scratch + lbm::kScratchErrOffset); }
 double *partials(lbm_ctx *c) { return (double *)((char *)c->scratch + lbm::kScratchPartialOffset); }
@@ -108,7 +127,7 @@ cudaError_t timed(lbm_ctx *c, int kind, F &&launch) {
 
 lbm_status refresh_psi(lbm_ctx *c) {
   if (c->psi_valid) return LBM_OK;
-  CK(lbm::launch_psi(c->P, c->precision, c->g[c->cur], c->psi, err_word(c), c->L), "psi kernel");
+  CK(lbm::launch_psi(c->P, c->precision, c->g[c->cur], cur_psi(c), err_word(c), c->L), "psi kernel");
   c->psi_valid = true;
   return LBM_OK;
 }
@@ -150,7 +169,8 @@ lbm_status lbm_create(const int grid[3], const lbm_eos *eos, double G, const lbm
   if (!grid || !eos || !rates) return LBM_ERR_ARG;
   if (grid[0] < 3 || grid[1] < 3 || grid[2] < 3) return LBM_ERR_ARG;
   const long long n = (long long)grid[0] * grid[1] * grid[2];
-  if (n >= (1LL << 31) || grid[2] > 65535) return LBM_ERR_ARG;  // 32-bit node index; grid.z
+  // 32-bit node index, unsigned 32-bit element offsets (19 N < 2^32), grid.z limit
+  if (n >= (1LL << 31) || 19 * n >= (1LL << 32) || grid[2] > 65535) return LBM_ERR_ARG;
   if (op != LBM_OP_ORTHOGONAL && op != LBM_OP_NONORTHOGONAL) return LBM_ERR_ARG;
   if (precision < LBM_F64 || precision > LBM_F32_STORE_F16) return LBM_ERR_ARG;
   if (eos->kind < LBM_EOS_CS || eos->kind > LBM_EOS_NONE) return LBM_ERR_ARG;
@@ -209,6 +229,7 @@ lbm_status lbm_create(const int grid[3], const lbm_eos *eos, double G, const lbm
   c->L.stream = (cudaStream_t)cuda_stream;
   c->L.bx = 32;
   c->L.by = 4;
+  c->onepass = false;  // the two-pass step is the faster default (see lbm_set_tuning)
   *out = c;
   return LBM_OK;
 }
@@ -320,16 +341,37 @@ lbm_status lbm_step(lbm_ctx *c, int n) {
   if (!c) return LBM_ERR_ARG;
   if (n < 1) return fail(c, LBM_ERR_ARG, "n must be >= 1");
   if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_step before an init");
+  if (c->onepass && !c->psi_valid) {
+    CK(timed(c, 0, [&] {
+         return lbm::launch_psi(c->P, c->precision, c->g[c->cur], cur_psi(c), err_word(c), c->L);
+       }),
+       "psi kernel");
+    c->psi_valid = true;
+  }
+  const int zc = c->zc > 0 ? c->zc : auto_zc(c);
   for (int k = 0; k < n; ++k) {
     void *gin = c->g[c->cur], *gout = c->g[c->cur ^ 1];
-    CK(timed(c, 0, [&] { return lbm::launch_psi(c->P, c->precision, gin, c->psi, err_word(c), c->L); }),
-       "psi kernel");
-    CK(timed(c, 1, [&] {
-         return lbm::launch_fused(c->P, c->precision, c->op, c->sigma_on, gin, gout, c->psi, c->L);
-       }),
-       "fused kernel");
-    c->cur ^= 1;
-    c->psi_valid = false;
+    if (c->onepass) {
+      void *pin = cur_psi(c), *pout = psi_at(c, c->pc ^ 1);
+      CK(timed(c, 1, [&] {
+           return lbm::launch_onepass(c->P, c->precision, c->op, c->sigma_on, c->tile, zc, gin, gout, pin, pout,
+                                      err_word(c), c->L.stream);
+         }),
+         "single-pass kernel");
+      c->pc ^= 1;
+      c->cur ^= 1;
+      c->psi_valid = true;
+    } else {
+      void *psi = cur_psi(c);
+      CK(timed(c, 0, [&] { return lbm::launch_psi(c->P, c->precision, gin, psi, err_word(c), c->L); }),
+         "psi kernel");
+      CK(timed(c, 1, [&] {
+           return lbm::launch_fused(c->P, c->precision, c->op, c->sigma_on, gin, gout, psi, c->L);
+         }),
+         "fused kernel");
+      c->cur ^= 1;
+      c->psi_valid = false;
+    }
     ++c->steps;
     if (c->check_interval > 0 && c->steps % c->check_interval == 0) {
       lbm_status s = lbm_check(c);
@@ -346,11 +388,11 @@ lbm_status lbm_moments(lbm_ctx *c, double *rho, double *u, int on_device) {
   if (s != LBM_OK) return s;
   const size_t n = c->P.n;
   if (on_device) {
-    CK(lbm::launch_moments(c->P, c->precision, c->g[c->cur], c->psi, rho, u, c->L), "moments kernel");
+    CK(lbm::launch_moments(c->P, c->precision, c->g[c->cur], cur_psi(c), rho, u, c->L), "moments kernel");
     return LBM_OK;
   }
   double *tmp = (double *)spare(c);  // 4N doubles fit in any population buffer
-  CK(lbm::launch_moments(c->P, c->precision, c->g[c->cur], c->psi, tmp, tmp + n, c->L), "moments kernel");
+  CK(lbm::launch_moments(c->P, c->precision, c->g[c->cur], cur_psi(c), tmp, tmp + n, c->L), "moments kernel");
   if (rho) CK(cudaMemcpyAsync(rho, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->L.stream), "D2H rho");
   if (u) CK(cudaMemcpyAsync(u, tmp + n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->L.stream), "D2H u");
   CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
@@ -400,7 +442,7 @@ lbm_status lbm_diag(lbm_ctx *c, double out[5]) {
   if (!c->initialized) return fail(c, LBM_ERR_STATE, "no state");
   lbm_status s = refresh_psi(c);
   if (s != LBM_OK) return s;
-  CK(lbm::launch_diag(c->P, c->precision, c->g[c->cur], c->psi, partials(c), result(c), c->L), "diag kernels");
+  CK(lbm::launch_diag(c->P, c->precision, c->g[c->cur], cur_psi(c), partials(c), result(c), c->L), "diag kernels");
   CK(cudaMemcpyAsync(out, result(c), 5 * sizeof(double), cudaMemcpyDeviceToHost, c->L.stream), "D2H diag");
   CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
   return LBM_OK;
@@ -435,6 +477,24 @@ lbm_status lbm_kernel_times(lbm_ctx *c, double *ms_psi, long long *n_psi, double
   if (n_psi) *n_psi = cnt[0];
   if (ms_fused) *ms_fused = t[1];
   if (n_fused) *n_fused = cnt[1];
+  return LBM_OK;
+}
+
+lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
+  if (!c || tile < 0 || tile > 2 || z_planes < 0) return fail(c, LBM_ERR_ARG, "bad tuning");
+  if (single_pass && c->precision == LBM_F64) return fail(c, LBM_ERR_ARG, "single pass needs FP32 arithmetic");
+  if (c->onepass != (single_pass != 0)) c->psi_valid = false;
+  c->onepass = single_pass != 0;
+  c->tile = tile;
+  c->zc = z_planes;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_tuning(const lbm_ctx *c, int *single_pass, int *tile, int *z_planes) {
+  if (!c) return LBM_ERR_ARG;
+  if (single_pass) *single_pass = c->onepass ? 1 : 0;
+  if (tile) *tile = c->tile;
+  if (z_planes) *z_planes = c->zc > 0 ? c->zc : auto_zc(c);
   return LBM_OK;
 }
 

@@ -86,18 +86,21 @@ template <typename S> struct Storage;
 
 template <> struct Storage<double> {
   using Compute = double;
+  static __device__ __forceinline__ double decode(double v, int a) { (void)a; return v; }
   static __device__ __forceinline__ double load(const double *p, int a) { (void)a; return __ldg(p); }
   static __device__ __forceinline__ void store(double *p, int a, double v) { (void)a; *p = v; }
 };
 
 template <> struct Storage<float> {
   using Compute = float;
+  static __device__ __forceinline__ float decode(float v, int a) { (void)a; return v; }
   static __device__ __forceinline__ float load(const float *p, int a) { (void)a; return __ldg(p); }
   static __device__ __forceinline__ void store(float *p, int a, float v) { (void)a; *p = v; }
 };
 
 template <> struct Storage<__half> {
   using Compute = float;
+  static __device__ __forceinline__ float decode(__half v, int a) { return __half2float(v) * (float)lattice_w(a); }
   static __device__ __forceinline__ float load(const __half *p, int a) {
     return __half2float(__ldg(p)) * (float)lattice_w(a);
   }

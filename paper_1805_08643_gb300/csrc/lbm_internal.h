@@ -72,6 +72,15 @@ inline void refresh_float_params(KParams &P) {
   P.fb4 = (float)P.b4;
 }
 
+// x-y tile shapes of the single-pass kernel.
+enum Tile { kTile32x4 = 0, kTile32x8 = 1, kTile64x4 = 2 };
+
+// Single-pass step (FP32 and FP16-storage forms): reads populations g_in and
+// psi(t) from psi_in, writes populations g_out and psi(t+1) to psi_out.  zc is
+// the number of z planes each CTA marches through.
+cudaError_t launch_onepass(const KParams &P, int precision, int op, bool sigma, int tile, int zc, const void *g_in,
+                           void *g_out, const void *psi_in, void *psi_out, unsigned *err, cudaStream_t s);
+
 size_t storage_bytes(int precision);  // bytes per stored population
 size_t psi_elem_bytes(int precision);
 

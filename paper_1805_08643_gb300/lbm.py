@@ -57,6 +57,8 @@ SIGNATURES = {
     "lbm_set_check_interval": (_c_int, [_vp, _c_int]),
     "lbm_set_profiling": (_c_int, [_vp, _c_int]),
     "lbm_kernel_times": (_c_int, [_vp, _dp, _llp, _dp, _llp]),
+    "lbm_set_tuning": (_c_int, [_vp, _c_int, _c_int, _c_int]),
+    "lbm_get_tuning": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "lbm_step_count": (ctypes.c_longlong, [_vp]),
     "lbm_step_static": (_c_int, [_vp, _vp, _vp]),
     "lbm_destroy": (None, [_vp]),
@@ -235,6 +237,14 @@ class Lattice:
 
     def set_check_interval(self, k):
         self._check(lib.lbm_set_check_interval(self._h, int(k)), "lbm_set_check_interval")
+
+    def set_tuning(self, single_pass=True, tile=1, z_planes=0):
+        self._check(lib.lbm_set_tuning(self._h, int(bool(single_pass)), int(tile), int(z_planes)), "lbm_set_tuning")
+
+    def tuning(self):
+        sp, t, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib.lbm_get_tuning(self._h, ctypes.byref(sp), ctypes.byref(t), ctypes.byref(z)), "lbm_get_tuning")
+        return {"single_pass": bool(sp.value), "tile": t.value, "z_planes": z.value}
 
     def set_profiling(self, on=True):
         self._check(lib.lbm_set_profiling(self._h, 1 if on else 0), "lbm_set_profiling")

@@ -1,0 +1,96 @@
+"""The FP32-arithmetic forms against the FP64 oracle, and the single-pass kernel.
+
+Tolerances (200 steps of the 32^3 droplet workload, rho_L = 0.31):
+* FP32 arithmetic and storage.  Unit round-off u = 2^-24; a node's density sums
+  19 stored values, each rounded once per step, so per step |d rho| ~ 19 u rho_L
+  and over n steps a random walk gives ~ sqrt(n) 19 u rho_L = 5e-6.  The test
+  allows 4x that: 2e-5 in rho and, with |u| errors of the same order divided by
+  rho >= rho_V, 2e-5 in u (measured: 1.6e-6 and 2.1e-7).
+* FP16 storage (FP32 arithmetic).  Stored values are (f - w rho_ref)/w, of size
+  up to rho_L - rho_V = 0.29, rounded to u16 = 2^-11: per step |d rho| ~
+  sqrt(19) w 0.29 u16 / 2 ~ 3e-5 and sqrt(200) times that is 4.6e-4; allowed
+  2e-3 in rho and u (measured: 3.1e-4 and 1.6e-4).
+"""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import coexistence, droplet_rho, lattice, max_abs, oracle_params, physics
+from oracle import lbm_oracle as L
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 2e-5, "f16": 2e-3}
+OPS = ["nonorth", "orth"]
+
+
+@pytest.fixture(scope="module")
+def oracle_runs():
+    cache = {}
+
+    def get(grid, op, steps=200):
+        key = (grid, op, steps)
+        if key not in cache:
+            phys = physics(T_over_Tc=0.8)
+            rl, rv = coexistence(0.8)
+            c = tuple(n / 2 for n in grid)
+            p = oracle_params(grid, op, phys)
+            f = L.run(p, L.equilibrium_state(p, droplet_rho(grid, c, 8.0, 2.0, rl, rv)), steps)
+            cache[key] = L.macroscopic(p, f)[:2]
+        return cache[key]
+
+    return get
+
+
+def _run(grid, op, prec, steps, single_pass=True, tile=1, zc=0):
+    phys = physics(T_over_Tc=0.8)
+    rl, rv = coexistence(0.8)
+    lat = lattice(grid, op, prec, phys)
+    lat.set_tuning(single_pass, tile, zc)
+    lat.init_droplet(tuple(n / 2 for n in grid), 8.0, 2.0, rl, rv)
+    d0 = lat.diag()
+    lat.step(steps)
+    d1 = lat.diag()
+    rho, u = lat.moments()
+    st = lat.check()
+    lat.close()
+    return rho, u, d0, d1, st
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("op", OPS)
+@pytest.mark.parametrize("grid", [(32, 32, 32), (24, 20, 28)])
+@pytest.mark.parametrize("single_pass", [True, False])
+def test_reduced_precision_against_fp64_oracle(oracle_runs, prec, op, grid, single_pass):
+    rho_o, u_o = oracle_runs(grid, op)
+    rho, u, d0, d1, st = _run(grid, op, prec, 200, single_pass)
+    assert st == 0
+    err_r, err_u = max_abs(rho, rho_o), max_abs(u, u_o)
+    print(f"{prec} {op} {grid} single_pass={single_pass}: |drho|={err_r:.2e} |du|={err_u:.2e} "
+          f"mass drift={(d1['mass'] - d0['mass']) / d0['mass']:.2e}")
+    assert err_r <= TOL[prec] and err_u <= TOL[prec]
+    assert abs(d1["mass"] - d0["mass"]) <= 20 * TOL[prec] * d0["mass"] / 19
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_single_pass_independent_of_tile_and_chunking(prec):
+    ref = None
+    for tile in (0, 1, 2):
+        for zc in (0, 5, 11, 30):
+            phys = physics()
+            rl, rv = coexistence(0.8)
+            lat = lattice((40, 36, 30), "nonorth", prec, phys)
+            lat.set_tuning(True, tile, zc)
+            lat.init_droplet((20.0, 18.0, 15.0), 8.0, 2.0, rl, rv)
+            lat.step(25)
+            rho, u = lat.moments()
+            lat.close()
+            if ref is None:
+                ref = (rho, u)
+            assert np.array_equal(rho, ref[0]) and np.array_equal(u, ref[1]), (tile, zc)
+
+
+def test_single_pass_matches_two_pass_fp32():
+    a = _run((32, 32, 32), "nonorth", "f32", 100, single_pass=True)
+    b = _run((32, 32, 32), "nonorth", "f32", 100, single_pass=False)
+    assert max_abs(a[0], b[0]) < 1e-6 and max_abs(a[1], b[1]) < 1e-6
