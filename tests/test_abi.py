@@ -66,10 +66,10 @@ def test_create_validates_arguments_without_touching_the_gpu(lbm):
     assert lbm.lib.lbm_step_count(h) == 0
     pb, sb, xb = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
     assert lbm.lib.lbm_buffer_bytes(h, ctypes.byref(pb), ctypes.byref(sb), ctypes.byref(xb)) == lbm.OK
-    assert pb.value == 19 * 512 * 8 and sb.value == 512 * 8
+    assert pb.value == 19 * 512 * 8 and sb.value == 2 * 512 * 8  # two psi time levels
     lbm.lib.lbm_destroy(h)
     st, h = _create(lbm, prec=2)
     lbm.lib.lbm_buffer_bytes(h, ctypes.byref(pb), ctypes.byref(sb), ctypes.byref(xb))
-    assert pb.value == 19 * 512 * 2 and sb.value == 512 * 4
+    assert pb.value == 19 * 512 * 2 and sb.value == 2 * 512 * 4
     lbm.lib.lbm_destroy(h)
     assert lbm.lib.lbm_status_string(4) == b"LBM_ERR_NONFINITE"
