@@ -51,6 +51,8 @@ FUSED_BYTES = {"f64": 19 * 8 * 2 + 8, "f32": 19 * 4 * 2 + 4, "f16": 19 * 2 * 2 +
 # ... and of the psi pass: 19 populations read + psi written
 PSI_BYTES = {"f64": 19 * 8 + 8, "f32": 19 * 4 + 4, "f16": 19 * 2 + 4}
 HEADLINE = ("nonorth", "f32")
+PREC_TEXT = {"f64": "FP64 compute and storage", "f32": "FP32 compute and storage",
+             "f16": "FP32 compute, FP16 storage"}
 
 
 def peaks():
@@ -173,11 +175,13 @@ def make_lattice(op, prec, edge, sigma=SIGMA_DROPLET):
     return lat, rl, rv
 
 
-def time_form(op, prec, edge, steps, warmup, world, clocks_index=None, field="droplet"):
+def time_form(op, prec, edge, steps, warmup, world, clocks_index=None, field="droplet", single_pass=False):
     """Device-timed steps of one form; returns (ms_per_step, kernel times, clocks)."""
     import torch
 
     lat, rl, rv = make_lattice(op, prec, edge, SIGMA_DROPLET if field == "droplet" else SIGMA_FLAT)
+    if single_pass:
+        lat.set_tuning(True, 1, 0)
     if field == "droplet":
         lat.init_droplet((edge / 2,) * 3, 40.0 * edge / 256, W_DROPLET, rl, rv)
     else:
@@ -304,8 +308,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--edge", type=int, default=EDGE)
+    ap.add_argument("--op", default=HEADLINE[0], choices=["nonorth", "orth"])
+    ap.add_argument("--prec", default=HEADLINE[1], choices=["f64", "f32", "f16"])
+    ap.add_argument("--single-pass", type=int, default=0, help="1: single-pass kernel (FP32 arithmetic forms)")
     ap.add_argument("--forms", default="all", help="'all' or 'headline'")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -323,8 +331,9 @@ def main():
     n = args.edge ** 3
     hbm_peak, peak_kind = peaks()
 
-    op, prec = HEADLINE
-    ms, kt, clocks, status = time_form(op, prec, args.edge, args.steps, args.warmup, world, clocks_index=local)
+    op, prec = args.op, args.prec
+    ms, kt, clocks, status = time_form(op, prec, args.edge, args.steps, args.warmup, world, clocks_index=local,
+                                       single_pass=bool(args.single_pass))
     ms = max_over_ranks(ms, world)
     ms_step = ms / args.steps
     value = sum_over_ranks(n * args.steps / (ms / 1e3) / 1e6, world)  # all ranks' nodes / max time
@@ -361,9 +370,13 @@ def main():
                                              "hbm_frac_fused": FUSED_BYTES[fprec] * n / (f_fused / 1e3) / 1e9 / hbm_peak,
                                              "status": fst}
 
-    e2e_steps = args.steps
-    t_e2e, h2d, d2h = e2e_run(op, prec, args.edge, e2e_steps)
-    e2e_val = sum_over_ranks(n * e2e_steps / max_over_ranks(t_e2e, world) / 1e6, world)
+    e2e = None
+    if not args.no_e2e:
+        e2e_steps = args.steps
+        t_e2e, h2d, d2h = e2e_run(op, prec, args.edge, e2e_steps)
+        e2e = {"value": sum_over_ranks(n * e2e_steps / max_over_ranks(t_e2e, world) / 1e6, world), "unit": UNIT,
+               "h2d_bytes_per_step": h2d / e2e_steps, "d2h_bytes_per_step": d2h / e2e_steps,
+               "note": "lbm_init_field from pinned host rho, lbm_step(K), lbm_moments to pinned host"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -374,9 +387,10 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic",
         "config": {"workload": f"D3Q19 non-orthogonal MRT + CS pseudopotential, {args.edge}^3 periodic box, "
-                               f"droplet R={40.0 * args.edge / 256:g} W=5, T=0.7Tc, sigma=0.105 (Eq. 16), FP32 compute and storage",
+                               f"droplet R={40.0 * args.edge / 256:g} W=5, T=0.7Tc, sigma=0.105 (Eq. 16), "
+                               f"{op} operator, {PREC_TEXT[prec]}",
                    "edge": args.edge, "operator": op, "precision": prec,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (populations 1.27 GB per buffer)"},
@@ -385,9 +399,7 @@ def main():
                      "kernel": "fused force+collide+stream", "bytes_per_node": FUSED_BYTES[prec],
                      "fused_ms": fused_ms, "psi_ms": psi_ms},
         "clocks": clocks,
-        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d / e2e_steps,
-                "d2h_bytes_per_step": d2h / e2e_steps,
-                "note": "lbm_init_field from pinned host rho, lbm_step(K), lbm_moments to pinned host"},
+        "e2e": e2e,
         "gpu_launches": 2 * args.steps,
         "forms": forms,
         "status": status,
