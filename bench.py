@@ -51,6 +51,13 @@ FUSED_BYTES = {"f64": 19 * 8 * 2 + 8, "f32": 19 * 4 * 2 + 4, "f16": 19 * 2 * 2 +
 # ... and of the psi pass: 19 populations read + psi written
 PSI_BYTES = {"f64": 19 * 8 + 8, "f32": 19 * 4 + 4, "f16": 19 * 2 + 4}
 HEADLINE = ("nonorth", "f32")
+# DRAM bytes per node of the fused pass from one ncu capture at 256^3 (profiles/fused_psi_nonorth_f32.md);
+# null for forms without a capture of the current kernel.
+FUSED_DRAM_BYTES = {("nonorth", "f32"): 153.3}
+# FP64 instructions per node of the fused pass (ncu, profiles/fused_psi_nonorth_orth_f64.md) and the FP64
+# issue peak of one GB300: 2 per SM per clock x 152 SMs x 2070 MHz.
+FUSED_FP64_INSTR = {"nonorth": 255.0, "orth": 309.0}
+FP64_PEAK_GINSTR = 2 * 152 * 2070e6 / 1e9
 PREC_TEXT = {"f64": "FP64 compute and storage", "f32": "FP32 compute and storage",
              "f16": "FP32 compute, FP16 storage"}
 
@@ -341,6 +348,18 @@ def main():
     psi_ms = kt["psi_ms"] / max(kt["psi_launches"], 1)
     achieved = FUSED_BYTES[prec] * n / (fused_ms / 1e3) / 1e9
 
+    if prec == "f64":
+        ach = FUSED_FP64_INSTR[op] * n / (fused_ms / 1e3) / 1e9
+        roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GINSTR, "unit": "G FP64 instr/s",
+                    "frac": ach / FP64_PEAK_GINSTR, "traffic": None, "peak_kind": "derived: 2 FP64/SM/clk x 152 x 2070 MHz",
+                    "kernel": "fused force+collide+stream", "fp64_instr_per_node": FUSED_FP64_INSTR[op],
+                    "fused_ms": fused_ms, "psi_ms": psi_ms}
+    else:
+        dram = FUSED_DRAM_BYTES.get((op, prec)) if args.edge == EDGE and not args.single_pass else None
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": dram * n if dram else None,
+                    "peak_kind": peak_kind, "kernel": "single pass" if args.single_pass else "fused force+collide+stream",
+                    "bytes_per_node": FUSED_BYTES[prec], "fused_ms": fused_ms, "psi_ms": psi_ms}
     forms = {}
     if args.forms == "all":
         for fop in ("nonorth", "orth"):
@@ -350,7 +369,10 @@ def main():
                 f_fused = fkt["fused_ms"] / max(fkt["fused_launches"], 1)
                 f_psi = fkt["psi_ms"] / max(fkt["psi_launches"], 1)
                 step_bytes = (FUSED_BYTES[fprec] + PSI_BYTES[fprec]) * n
-                forms[f"{fop}_{fprec}_droplet"] = {
+                extra = {}
+                if fprec == "f64":
+                    extra["fp64_alu_frac_fused"] = FUSED_FP64_INSTR[fop] * n / (f_fused / 1e3) / 1e9 / FP64_PEAK_GINSTR
+                forms[f"{fop}_{fprec}_droplet"] = {**extra,
                     "mlups": n * steps_f / (fms / 1e3) / 1e6,
                     "ms_per_step": fms / steps_f,
                     "fused_ms": f_fused, "psi_ms": f_psi,
@@ -394,10 +416,7 @@ def main():
                    "edge": args.edge, "operator": op, "precision": prec,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs larger than L2 (populations 1.27 GB per buffer)"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "fused force+collide+stream", "bytes_per_node": FUSED_BYTES[prec],
-                     "fused_ms": fused_ms, "psi_ms": psi_ms},
+        "roofline": roofline,
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,
