@@ -192,6 +192,72 @@ long long lbm_step_count(const lbm_ctx *ctx);
  * Errors: LBM_ERR_ARG (null or aliased pointers, precision, size), LBM_ERR_CUDA. */
 lbm_status lbm_step_static(const lbm_ctx *ctx, const double *f_in, double *f_out);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent periodic boxes advanced together: every step is one
+ * persistent launch of the single-pass kernel over a table of work items
+ * (one x-y tile of one box and a range of z planes each, largest boxes first),
+ * and lbm_batch_step replays the launches of two steps as a CUDA graph.  Boxes
+ * may differ in size, operator, temperature, G, rates and sigma; they share the
+ * precision (LBM_F32 or LBM_F32_STORE_F16) and the kind of EOS.  Boxes join
+ * (lbm_batch_add) and leave (lbm_batch_remove) between calls: continuous
+ * batching.  Each box's buffers come from the stream-ordered allocator of the
+ * batch's stream and are charged to the batch's HBM budget (admission by
+ * footprint).  A box's results do not depend on the other boxes of the batch.
+ * Not in the paper: the paper steps one box at a time. */
+typedef struct lbm_batch lbm_batch;
+
+/* Device bytes one box of the given size holds in a batch (populations, two
+ * psi levels, the previous velocity for lbm_batch_max_du); 0 for a bad grid. */
+size_t lbm_batch_box_bytes(int precision, const int grid[3]);
+
+/* precision: LBM_F32 or LBM_F32_STORE_F16; eos_kind: lbm_eos_kind shared by all
+ * boxes; hbm_budget_bytes: the most device memory the boxes may hold;
+ * cuda_stream: a cudaStream_t (NULL: the batch creates its own stream). */
+lbm_status lbm_batch_create(int precision, int eos_kind, size_t hbm_budget_bytes, void *cuda_stream,
+                            lbm_batch **out);
+
+/* Add a box (parameters as in lbm_create); *id receives its handle.  Errors:
+ * LBM_ERR_ARG, LBM_ERR_OOM when the budget or the device has no room. */
+lbm_status lbm_batch_add(lbm_batch *b, const int grid[3], const lbm_eos *eos, double G, const lbm_rates *rates,
+                         int op, double sigma, int *id);
+lbm_status lbm_batch_remove(lbm_batch *b, int id);
+
+/* Initial states of one box, as lbm_init_droplet / lbm_init_flat.  A box takes
+ * part in lbm_batch_step once it has been initialised. */
+lbm_status lbm_batch_init_droplet(lbm_batch *b, int id, const double centre[3], double R, double W,
+                                  double rho_l, double rho_v);
+lbm_status lbm_batch_init_flat(lbm_batch *b, int id, int axis, double lo, double hi, double W, double rho_l,
+                               double rho_v);
+
+/* Tile shape of the batch (0: 32x4, 1: 32x8, 2: 64x4) and, for box id >= 0, its
+ * z planes per work item (0 = automatic).  Results do not depend on either. */
+lbm_status lbm_batch_set_tuning(lbm_batch *b, int tile, int id, int z_planes);
+
+/* Advance every initialised box n >= 1 steps (even n replays the two-step graph
+ * only; an odd n also re-uploads the box table). */
+lbm_status lbm_batch_step(lbm_batch *b, int n);
+
+/* Per-box observables, as lbm_moments and lbm_diag. */
+lbm_status lbm_batch_moments(lbm_batch *b, int id, double *rho, double *u, int on_device);
+lbm_status lbm_batch_diag(lbm_batch *b, int id, double out[5]);
+
+/* For the nid boxes in ids: out[k] = max over nodes of |u(t) - u(t_prev)|, where
+ * t_prev is the previous call for that box (or its initialisation: u = 0),
+ * FP64; host output, synchronises.  Used as the convergence test of a job. */
+lbm_status lbm_batch_max_du(lbm_batch *b, int nid, const int *ids, double *out);
+
+/* Read and clear the batch's device error word (as lbm_check). */
+lbm_status lbm_batch_check(lbm_batch *b);
+
+/* Live boxes, work items of the current table, device bytes charged. */
+lbm_status lbm_batch_info(const lbm_batch *b, int *live_boxes, int *work_items, size_t *bytes_used);
+
+/* Steps box id has taken since its initialisation (-1: no such box). */
+long long lbm_batch_box_steps(const lbm_batch *b, int id);
+
+const char *lbm_batch_last_error(const lbm_batch *b);
+void lbm_batch_destroy(lbm_batch *b);
+
 /* Release the context and any device memory it allocated itself. */
 void lbm_destroy(lbm_ctx *ctx);
 

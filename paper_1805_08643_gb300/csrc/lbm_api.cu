@@ -15,6 +15,11 @@
 
 using lbm::KParams;
 
+namespace lbm {
+bool fill_params(const int grid[3], const lbm_eos *eos, double G, const lbm_rates *rates, int op, int precision,
+                 double sigma, KParams *out);
+}
+
 struct lbm_ctx {
   KParams P{};
   int precision = 0, op = 1;
@@ -166,63 +171,11 @@ lbm_status lbm_create(const int grid[3], const lbm_eos *eos, double G, const lbm
                       int precision, double sigma, void *cuda_stream, lbm_ctx **out) {
   if (!out) return LBM_ERR_ARG;
   *out = nullptr;
-  if (!grid || !eos || !rates) return LBM_ERR_ARG;
-  if (grid[0] < 3 || grid[1] < 3 || grid[2] < 3) return LBM_ERR_ARG;
-  const long long n = (long long)grid[0] * grid[1] * grid[2];
-  // 32-bit node index, unsigned 32-bit element offsets (19 N < 2^32), grid.z limit
-  if (n >= (1LL << 31) || 19 * n >= (1LL << 32) || grid[2] > 65535) return LBM_ERR_ARG;
-  if (op != LBM_OP_ORTHOGONAL && op != LBM_OP_NONORTHOGONAL) return LBM_ERR_ARG;
-  if (precision < LBM_F64 || precision > LBM_F32_STORE_F16) return LBM_ERR_ARG;
-  if (eos->kind < LBM_EOS_CS || eos->kind > LBM_EOS_NONE) return LBM_ERR_ARG;
-  const double rs[6] = {rates->s_e, rates->s_nu, rates->s_q, rates->s_pi, rates->s_eps, rates->s_m};
-  for (double s : rs)
-    if (!(s > 0.0 && s < 2.0)) return LBM_ERR_ARG;  // stable range of a relaxation rate
-  if (!std::isfinite(G) || !std::isfinite(sigma)) return LBM_ERR_ARG;
-  if (eos->kind == LBM_EOS_CS) {
-    if (!finite_positive(eos->b) || !finite_positive(eos->R) || !finite_positive(eos->T) ||
-        !std::isfinite(eos->a) || G == 0.0)
-      return LBM_ERR_ARG;
-  } else if (eos->kind == LBM_EOS_EXP) {
-    if (!std::isfinite(eos->psi0) || !finite_positive(eos->rho0)) return LBM_ERR_ARG;
-  }
-  if (sigma != 0.0 && eos->kind == LBM_EOS_NONE) return LBM_ERR_ARG;
-
+  KParams P;
+  if (!lbm::fill_params(grid, eos, G, rates, op, precision, sigma, &P)) return LBM_ERR_ARG;
   lbm_ctx *c = new (std::nothrow) lbm_ctx();
   if (!c) return LBM_ERR_OOM;
-  KParams &P = c->P;
-  P.nx = grid[0];
-  P.ny = grid[1];
-  P.nz = grid[2];
-  P.n = (int)n;
-  P.G = eos->kind == LBM_EOS_NONE ? 0.0 : G;
-  P.rho_ref = 0.0;
-  P.s_e = rates->s_e;
-  P.s_nu = rates->s_nu;
-  P.s_q = rates->s_q;
-  P.s_pi = rates->s_pi;
-  P.s_eps = rates->s_eps;
-  P.s_m = rates->s_m;
-  P.sigma_coef = 6.0 * sigma * G * G / (1.0 / rates->s_e - 0.5);
-  P.eos = eos->kind;
-  P.a = eos->a;
-  P.b = eos->b;
-  P.RT = eos->R * eos->T;
-  P.psi0 = eos->psi0;
-  P.rho0 = eos->rho0;
-  P.b4 = 0.25 * eos->b;
-  P.two_over_G = P.G != 0.0 ? 2.0 / P.G : 0.0;
-  {
-    // coefficients of the radicand polynomial (see KParams)
-    const double cc = P.b4, rt = P.RT, aa = P.a, k = P.two_over_G;
-    P.q0 = k * (rt - 1.0 / 3.0);
-    P.q1 = k * (rt * cc - aa + cc);
-    P.q2 = k * (rt * cc * cc + 3.0 * aa * cc - cc * cc);
-    P.q3 = k * (-rt * cc * cc * cc - 3.0 * aa * cc * cc + cc * cc * cc / 3.0);
-    P.q4 = k * (aa * cc * cc * cc);
-    P.f_rho_max = eos->b > 0 ? (float)(4.0 / eos->b) : 0.0f;
-  }
-  lbm::refresh_float_params(P);
-  lbm::refresh_float_params(P);
+  c->P = P;
   c->precision = precision;
   c->op = op;
   c->sigma_on = sigma != 0.0;
@@ -524,6 +477,69 @@ bool ctx_params(const lbm_ctx *c, KParams *P, int *precision, int *op, bool *sig
   *op = c->op;
   *sigma_on = c->sigma_on;
   *stream = c->L.stream;
+  return true;
+}
+}  // namespace lbm
+
+// Validate a box description and fill the kernel parameters (shared by
+// lbm_create and lbm_batch_add).
+namespace lbm {
+bool fill_params(const int grid[3], const lbm_eos *eos, double G, const lbm_rates *rates, int op, int precision,
+                 double sigma, KParams *out) {
+  if (!grid || !eos || !rates || !out) return false;
+  if (grid[0] < 3 || grid[1] < 3 || grid[2] < 3) return false;
+  const long long n = (long long)grid[0] * grid[1] * grid[2];
+  // 32-bit node index, unsigned 32-bit element offsets (19 N < 2^32), grid.z limit
+  if (n >= (1LL << 31) || 19 * n >= (1LL << 32) || grid[2] > 65535) return false;
+  if (op != LBM_OP_ORTHOGONAL && op != LBM_OP_NONORTHOGONAL) return false;
+  if (precision < LBM_F64 || precision > LBM_F32_STORE_F16) return false;
+  if (eos->kind < LBM_EOS_CS || eos->kind > LBM_EOS_NONE) return false;
+  const double rs[6] = {rates->s_e, rates->s_nu, rates->s_q, rates->s_pi, rates->s_eps, rates->s_m};
+  for (double s : rs)
+    if (!(s > 0.0 && s < 2.0)) return false;  // stable range of a relaxation rate
+  if (!std::isfinite(G) || !std::isfinite(sigma)) return false;
+  if (eos->kind == LBM_EOS_CS) {
+    if (!finite_positive(eos->b) || !finite_positive(eos->R) || !finite_positive(eos->T) || !std::isfinite(eos->a) ||
+        G == 0.0)
+      return false;
+  } else if (eos->kind == LBM_EOS_EXP) {
+    if (!std::isfinite(eos->psi0) || !finite_positive(eos->rho0)) return false;
+  }
+  if (sigma != 0.0 && eos->kind == LBM_EOS_NONE) return false;
+  KParams P{};
+  P.nx = grid[0];
+  P.ny = grid[1];
+  P.nz = grid[2];
+  P.n = (int)n;
+  P.G = eos->kind == LBM_EOS_NONE ? 0.0 : G;
+  P.rho_ref = 0.0;
+  P.s_e = rates->s_e;
+  P.s_nu = rates->s_nu;
+  P.s_q = rates->s_q;
+  P.s_pi = rates->s_pi;
+  P.s_eps = rates->s_eps;
+  P.s_m = rates->s_m;
+  P.sigma_coef = 6.0 * sigma * G * G / (1.0 / rates->s_e - 0.5);
+  P.eos = eos->kind;
+  P.a = eos->a;
+  P.b = eos->b;
+  P.RT = eos->R * eos->T;
+  P.psi0 = eos->psi0;
+  P.rho0 = eos->rho0;
+  P.b4 = 0.25 * eos->b;
+  P.two_over_G = P.G != 0.0 ? 2.0 / P.G : 0.0;
+  {
+    // coefficients of the radicand polynomial (see KParams)
+    const double cc = P.b4, rt = P.RT, aa = P.a, k = P.two_over_G;
+    P.q0 = k * (rt - 1.0 / 3.0);
+    P.q1 = k * (rt * cc - aa + cc);
+    P.q2 = k * (rt * cc * cc + 3.0 * aa * cc - cc * cc);
+    P.q3 = k * (-rt * cc * cc * cc - 3.0 * aa * cc * cc + cc * cc * cc / 3.0);
+    P.q4 = k * (aa * cc * cc * cc);
+    P.f_rho_max = eos->b > 0 ? (float)(4.0 / eos->b) : 0.0f;
+  }
+  refresh_float_params(P);
+  *out = P;
   return true;
 }
 }  // namespace lbm

@@ -1,0 +1,435 @@
+// Batched boxes: many independent periodic boxes advanced together, one
+// persistent single-pass launch per step over a table of work items, the
+// launches of two steps captured in a CUDA graph.  Boxes can join and leave
+// between calls (continuous batching); each box's buffers come from the
+// stream-ordered allocator and count against the batch's HBM budget.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+using lbm::BatchBox;
+using lbm::KParams;
+
+namespace lbm {
+bool fill_params(const int grid[3], const lbm_eos *eos, double G, const lbm_rates *rates, int op, int precision,
+                 double sigma, KParams *P);
+}
+
+namespace {
+
+struct HostBox {
+  bool live = false;
+  BatchBox d{};        // descriptor as the kernel sees it
+  int precision = 0;
+  bool initialised = false;
+  int zc = 0;          // planes per work item
+  size_t bytes = 0;    // device bytes held
+  void *mem = nullptr; // one allocation: g0, g1, psi0, psi1, u_prev
+  float *u_prev = nullptr;
+  long long steps = 0;
+};
+
+}  // namespace
+
+struct lbm_batch {
+  int precision = 1, eos = 0;
+  cudaStream_t stream = nullptr;
+  size_t budget = 0, used = 0;
+  int tile = lbm::kTile32x8;
+  int grid_blocks = 0;       // persistent grid size
+  std::vector<HostBox> boxes;
+  BatchBox *d_boxes = nullptr;
+  int4 *d_items = nullptr;
+  int cap_boxes = 0, cap_items = 0, nitems = 0;
+  unsigned *d_err = nullptr;
+  void *d_scratch = nullptr; // reduction partials of lbm_batch_diag
+  double *d_red = nullptr;   // per-box reduction results (max |du|)
+  bool own_stream = false;
+  int cap_red = 0;
+  bool dirty = true;         // descriptors / items need uploading, graphs re-capturing
+  cudaGraphExec_t g2 = nullptr, g1 = nullptr;
+  long long steps = 0;
+  std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch *b, lbm_status s, const std::string &m) {
+  if (b) b->err = m;
+  return s;
+}
+
+#define BCK(call, where)                                                                         \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return bfail(b, e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,               \
+                   std::string(where) + ": " + cudaGetErrorString(e_));                          \
+  } while (0)
+
+size_t box_bytes(int precision, long long n) {
+  const size_t pop = (size_t)19 * n * lbm::storage_bytes(precision);
+  auto up = [](size_t v) { return (v + 255) / 256 * 256; };
+  return 2 * up(pop) + 2 * up((size_t)n * 4) + up((size_t)3 * n * 4);
+}
+
+// Planes per work item unless tuned: 32 (two of them are recomputed).
+int default_zc(const KParams &P) { return std::min(P.nz, 32); }
+
+void destroy_graphs(lbm_batch *b) {
+  if (b->g2) cudaGraphExecDestroy(b->g2);
+  if (b->g1) cudaGraphExecDestroy(b->g1);
+  b->g2 = b->g1 = nullptr;
+}
+
+// Upload descriptors and the work-item table (largest boxes first), recapture graphs.
+lbm_status rebuild(lbm_batch *b) {
+  const int nb = (int)b->boxes.size();
+  if (nb > b->cap_boxes) {
+    if (b->d_boxes) cudaFreeAsync(b->d_boxes, b->stream);
+    BCK(cudaMallocAsync((void **)&b->d_boxes, sizeof(BatchBox) * std::max(nb, 1), b->stream), "box table");
+    b->cap_boxes = nb;
+  }
+  std::vector<BatchBox> desc(std::max(nb, 1));
+  std::vector<std::pair<long long, int>> order;
+  for (int i = 0; i < nb; ++i) {
+    desc[i] = b->boxes[i].d;
+    if (b->boxes[i].live && b->boxes[i].initialised) order.push_back({(long long)b->boxes[i].d.P.n, i});
+  }
+  std::sort(order.begin(), order.end(), [](auto &x, auto &y) { return x.first > y.first || (x.first == y.first && x.second < y.second); });
+  int bx, by;
+  lbm::onepass_tile_shape(b->tile, &bx, &by);
+  std::vector<int4> items;
+  for (auto &o : order) {
+    const HostBox &h = b->boxes[o.second];
+    const KParams &P = h.d.P;
+    const int tx = (P.nx + bx - 1) / bx, ty = (P.ny + by - 1) / by, zc = h.zc > 0 ? h.zc : default_zc(P);
+    for (int z0 = 0; z0 < P.nz; z0 += zc)
+      for (int j = 0; j < ty; ++j)
+        for (int i = 0; i < tx; ++i) items.push_back(make_int4(o.second, i | (j << 16), z0, std::min(z0 + zc, P.nz)));
+  }
+  if ((int)items.size() > b->cap_items) {
+    if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
+    BCK(cudaMallocAsync((void **)&b->d_items, sizeof(int4) * items.size(), b->stream), "item table");
+    b->cap_items = (int)items.size();
+  }
+  b->nitems = (int)items.size();
+  if (nb) BCK(cudaMemcpyAsync(b->d_boxes, desc.data(), sizeof(BatchBox) * nb, cudaMemcpyHostToDevice, b->stream), "H2D boxes");
+  if (b->nitems)
+    BCK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, b->stream), "H2D items");
+  BCK(cudaStreamSynchronize(b->stream), "sync");  // host vectors go out of scope
+  destroy_graphs(b);
+  if (b->nitems) {
+    const int per_sm = b->tile == lbm::kTile32x4 ? 4 : 2;  // resident blocks the kernel is sized for
+    const int grid = std::min(b->grid_blocks * per_sm, b->nitems);
+    for (int k = 0; k < 2; ++k) {
+      cudaGraph_t g;
+      BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+      cudaError_t e = lbm::launch_batch_onepass(b->precision, b->eos, b->tile, b->d_boxes, b->d_items, b->nitems, 0,
+                                                grid, b->d_err, b->stream);
+      if (e == cudaSuccess && k == 0)
+        e = lbm::launch_batch_onepass(b->precision, b->eos, b->tile, b->d_boxes, b->d_items, b->nitems, 1, grid,
+                                      b->d_err, b->stream);
+      cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (e2 == cudaSuccess) cudaGraphDestroy(g);
+        return bfail(b, LBM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+      }
+      cudaGraphExec_t x;
+      e = cudaGraphInstantiate(&x, g, 0);
+      cudaGraphDestroy(g);
+      BCK(e, "graph instantiate");
+      (k == 0 ? b->g2 : b->g1) = x;
+    }
+  }
+  b->dirty = false;
+  return LBM_OK;
+}
+
+HostBox *get_box(lbm_batch *b, int id) {
+  if (!b || id < 0 || id >= (int)b->boxes.size() || !b->boxes[id].live) return nullptr;
+  return &b->boxes[id];
+}
+
+lbm::Launch launch_of(lbm_batch *b) {
+  lbm::Launch L;
+  L.stream = b->stream;
+  L.bx = 32;
+  L.by = 4;
+  return L;
+}
+
+void *cur_g(HostBox *h) { return h->d.g[h->d.cur]; }
+float *cur_psi(HostBox *h) { return h->d.psi[h->d.cur]; }
+
+lbm_status finish_box_init(lbm_batch *b, HostBox *h, const double *rho_dev) {
+  const lbm::Launch L = launch_of(b);
+  BCK(lbm::launch_state_from_rho(h->d.P, h->precision, rho_dev, cur_g(h), L), "state_from_rho");
+  BCK(lbm::launch_psi(h->d.P, h->precision, cur_g(h), cur_psi(h), b->d_err, L), "psi");
+  BCK(cudaMemsetAsync(h->u_prev, 0, sizeof(float) * 3 * (size_t)h->d.P.n, b->stream), "clear u_prev");
+  h->initialised = true;
+  h->steps = 0;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_batch_box_bytes(int precision, const int grid[3]) {
+  if (!grid || grid[0] < 3 || grid[1] < 3 || grid[2] < 3) return 0;
+  return box_bytes(precision, (long long)grid[0] * grid[1] * grid[2]);
+}
+
+lbm_status lbm_batch_create(int precision, int eos_kind, size_t hbm_budget_bytes, void *cuda_stream,
+                            lbm_batch **out) {
+  if (!out) return LBM_ERR_ARG;
+  *out = nullptr;
+  if (precision != LBM_F32 && precision != LBM_F32_STORE_F16) return LBM_ERR_ARG;
+  if (eos_kind < LBM_EOS_CS || eos_kind > LBM_EOS_NONE) return LBM_ERR_ARG;
+  lbm_batch *b = new (std::nothrow) lbm_batch();
+  if (!b) return LBM_ERR_OOM;
+  b->precision = precision;
+  b->eos = eos_kind;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->budget = hbm_budget_bytes;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete b;
+    return LBM_ERR_CUDA;
+  }
+  b->grid_blocks = sms;
+  if (!b->stream) {  // graphs cannot be captured on the legacy default stream
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return LBM_ERR_CUDA;
+    }
+    b->own_stream = true;
+  }
+  if (cudaMallocAsync((void **)&b->d_err, 256, b->stream) != cudaSuccess ||
+      cudaMemsetAsync(b->d_err, 0, 256, b->stream) != cudaSuccess ||
+      cudaMallocAsync(&b->d_scratch, lbm::kScratchBytes, b->stream) != cudaSuccess) {
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return LBM_ERR_OOM;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_add(lbm_batch *b, const int grid[3], const lbm_eos *eos, double G, const lbm_rates *rates, int op,
+                         double sigma, int *id) {
+  if (!b || !id) return LBM_ERR_ARG;
+  if (!eos || eos->kind != b->eos) return bfail(b, LBM_ERR_ARG, "every box of a batch uses the batch's EOS kind");
+  KParams P;
+  if (!lbm::fill_params(grid, eos, G, rates, op, b->precision, sigma, &P)) return bfail(b, LBM_ERR_ARG, "bad box");
+  const size_t bytes = box_bytes(b->precision, P.n);
+  if (b->used + bytes > b->budget) return bfail(b, LBM_ERR_OOM, "HBM budget of the batch exceeded");
+  HostBox h;
+  BCK(cudaMallocAsync(&h.mem, bytes, b->stream), "box buffers");
+  const size_t pop = (((size_t)19 * P.n * lbm::storage_bytes(b->precision)) + 255) / 256 * 256;
+  const size_t ps = (((size_t)P.n * 4) + 255) / 256 * 256;
+  char *m = (char *)h.mem;
+  h.live = true;
+  h.precision = b->precision;
+  h.bytes = bytes;
+  h.d.P = P;
+  h.d.g[0] = m;
+  h.d.g[1] = m + pop;
+  h.d.psi[0] = (float *)(m + 2 * pop);
+  h.d.psi[1] = (float *)(m + 2 * pop + ps);
+  h.u_prev = (float *)(m + 2 * pop + 2 * ps);
+  h.d.op = op;
+  h.d.cur = 0;
+  b->used += bytes;
+  int slot = -1;
+  for (int i = 0; i < (int)b->boxes.size(); ++i)
+    if (!b->boxes[i].live) {
+      slot = i;
+      break;
+    }
+  if (slot < 0) {
+    slot = (int)b->boxes.size();
+    b->boxes.push_back(h);
+  } else {
+    b->boxes[slot] = h;
+  }
+  *id = slot;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_remove(lbm_batch *b, int id) {
+  HostBox *h = get_box(b, id);
+  if (!h) return bfail(b, LBM_ERR_ARG, "no such box");
+  cudaFreeAsync(h->mem, b->stream);
+  b->used -= h->bytes;
+  *h = HostBox();
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_init_droplet(lbm_batch *b, int id, const double centre[3], double R, double W, double rho_l,
+                                  double rho_v) {
+  HostBox *h = get_box(b, id);
+  if (!h || !centre || !(W > 0) || !(rho_l > 0) || !(rho_v > 0) || !(R >= 0)) return bfail(b, LBM_ERR_ARG, "bad droplet");
+  h->d.P.rho_ref = rho_v;
+  lbm::refresh_float_params(h->d.P);
+  lbm::DropletChunk ch{};
+  ch.count = 1;
+  ch.cx[0] = centre[0];
+  ch.cy[0] = centre[1];
+  ch.cz[0] = centre[2];
+  ch.r[0] = R;
+  double *rho = (double *)h->d.g[h->d.cur ^ 1];
+  BCK(lbm::launch_rho_droplets(h->d.P, rho, ch, W, rho_l, rho_v, true, launch_of(b)), "rho_droplets");
+  return finish_box_init(b, h, rho);
+}
+
+lbm_status lbm_batch_init_flat(lbm_batch *b, int id, int axis, double lo, double hi, double W, double rho_l,
+                               double rho_v) {
+  HostBox *h = get_box(b, id);
+  if (!h || axis < 0 || axis > 2 || !(lo < hi) || !(W > 0) || !(rho_l > 0) || !(rho_v > 0))
+    return bfail(b, LBM_ERR_ARG, "bad slab");
+  h->d.P.rho_ref = rho_v;
+  lbm::refresh_float_params(h->d.P);
+  double *rho = (double *)h->d.g[h->d.cur ^ 1];
+  BCK(lbm::launch_rho_slab(h->d.P, rho, axis, lo, hi, W, rho_l, rho_v, launch_of(b)), "rho_slab");
+  return finish_box_init(b, h, rho);
+}
+
+lbm_status lbm_batch_set_tuning(lbm_batch *b, int tile, int id, int z_planes) {
+  if (!b || tile < 0 || tile > 2 || z_planes < 0) return bfail(b, LBM_ERR_ARG, "bad tuning");
+  b->tile = tile;
+  if (id >= 0) {
+    HostBox *h = get_box(b, id);
+    if (!h) return bfail(b, LBM_ERR_ARG, "no such box");
+    h->zc = z_planes;
+  }
+  b->dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch *b, int n) {
+  if (!b || n < 1) return bfail(b, LBM_ERR_ARG, "n must be >= 1");
+  if (b->dirty) {
+    lbm_status s = rebuild(b);
+    if (s != LBM_OK) return s;
+  }
+  if (!b->nitems) return LBM_OK;
+  for (int k = 0; k + 1 < n; k += 2) BCK(cudaGraphLaunch(b->g2, b->stream), "graph launch");
+  if (n & 1) {
+    BCK(cudaGraphLaunch(b->g1, b->stream), "graph launch");
+    for (auto &h : b->boxes)
+      if (h.live && h.initialised) h.d.cur ^= 1;
+    b->dirty = true;  // descriptors changed: parity 0 now means the other level
+  }
+  for (auto &h : b->boxes)
+    if (h.live && h.initialised) h.steps += n;
+  b->steps += n;
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_moments(lbm_batch *b, int id, double *rho, double *u, int on_device) {
+  HostBox *h = get_box(b, id);
+  if (!h || !h->initialised || (!rho && !u)) return bfail(b, LBM_ERR_ARG, "bad box or output");
+  const lbm::Launch L = launch_of(b);
+  const size_t n = h->d.P.n;
+  if (on_device) {
+    BCK(lbm::launch_moments(h->d.P, h->precision, cur_g(h), cur_psi(h), rho, u, L), "moments");
+    return LBM_OK;
+  }
+  double *tmp = (double *)h->d.g[h->d.cur ^ 1];  // 4N doubles fit in a population buffer
+  BCK(lbm::launch_moments(h->d.P, h->precision, cur_g(h), cur_psi(h), tmp, tmp + n, L), "moments");
+  if (rho) BCK(cudaMemcpyAsync(rho, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, b->stream), "D2H rho");
+  if (u) BCK(cudaMemcpyAsync(u, tmp + n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, b->stream), "D2H u");
+  BCK(cudaStreamSynchronize(b->stream), "sync");
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_diag(lbm_batch *b, int id, double out[5]) {
+  HostBox *h = get_box(b, id);
+  if (!h || !h->initialised || !out) return bfail(b, LBM_ERR_ARG, "bad box or output");
+  double *part = (double *)((char *)b->d_scratch + lbm::kScratchPartialOffset);
+  double *res = (double *)((char *)b->d_scratch + lbm::kScratchResultOffset);
+  BCK(lbm::launch_diag(h->d.P, h->precision, cur_g(h), cur_psi(h), part, res, launch_of(b)), "diag");
+  BCK(cudaMemcpyAsync(out, res, 5 * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "D2H diag");
+  BCK(cudaStreamSynchronize(b->stream), "sync");
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_max_du(lbm_batch *b, int nid, const int *ids, double *out) {
+  if (!b || nid < 0 || (nid && (!ids || !out))) return bfail(b, LBM_ERR_ARG, "bad arguments");
+  if (nid > b->cap_red) {
+    if (b->d_red) cudaFreeAsync(b->d_red, b->stream);
+    BCK(cudaMallocAsync((void **)&b->d_red, sizeof(double) * nid, b->stream), "reduction buffer");
+    b->cap_red = nid;
+  }
+  if (!nid) return LBM_OK;
+  BCK(cudaMemsetAsync(b->d_red, 0, sizeof(double) * nid, b->stream), "clear");
+  for (int k = 0; k < nid; ++k) {
+    HostBox *h = get_box(b, ids[k]);
+    if (!h || !h->initialised) return bfail(b, LBM_ERR_ARG, "bad box id");
+    BCK(lbm::launch_max_du(h->d.P, h->precision, cur_g(h), cur_psi(h), h->u_prev, b->d_red + k, launch_of(b)),
+        "max_du");
+  }
+  BCK(cudaMemcpyAsync(out, b->d_red, sizeof(double) * nid, cudaMemcpyDeviceToHost, b->stream), "D2H");
+  BCK(cudaStreamSynchronize(b->stream), "sync");
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_check(lbm_batch *b) {
+  if (!b) return LBM_ERR_ARG;
+  unsigned w = 0;
+  BCK(cudaMemcpyAsync(&w, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream), "read error word");
+  BCK(cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream), "clear error word");
+  BCK(cudaStreamSynchronize(b->stream), "sync");
+  if (w & lbm::kErrNonFinite) return bfail(b, LBM_ERR_NONFINITE, "non-finite density");
+  if (w & lbm::kErrEosDomain) return bfail(b, LBM_ERR_EOS_DOMAIN, "density left the domain of the EOS");
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_info(const lbm_batch *b, int *live_boxes, int *work_items, size_t *bytes_used) {
+  if (!b) return LBM_ERR_ARG;
+  int live = 0;
+  for (auto &h : b->boxes) live += h.live ? 1 : 0;
+  if (live_boxes) *live_boxes = live;
+  if (work_items) *work_items = b->nitems;
+  if (bytes_used) *bytes_used = b->used;
+  return LBM_OK;
+}
+
+long long lbm_batch_box_steps(const lbm_batch *b, int id) {
+  if (!b || id < 0 || id >= (int)b->boxes.size() || !b->boxes[id].live) return -1;
+  return b->boxes[id].steps;
+}
+
+const char *lbm_batch_last_error(const lbm_batch *b) { return b ? b->err.c_str() : ""; }
+
+void lbm_batch_destroy(lbm_batch *b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  destroy_graphs(b);
+  for (auto &h : b->boxes)
+    if (h.live) cudaFreeAsync(h.mem, b->stream);
+  if (b->d_boxes) cudaFreeAsync(b->d_boxes, b->stream);
+  if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
+  if (b->d_red) cudaFreeAsync(b->d_red, b->stream);
+  if (b->d_err) cudaFreeAsync(b->d_err, b->stream);
+  if (b->d_scratch) cudaFreeAsync(b->d_scratch, b->stream);
+  cudaStreamSynchronize(b->stream);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+}  // extern "C"

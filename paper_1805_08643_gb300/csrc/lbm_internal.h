@@ -81,6 +81,25 @@ enum Tile { kTile32x4 = 0, kTile32x8 = 1, kTile64x4 = 2 };
 cudaError_t launch_onepass(const KParams &P, int precision, int op, bool sigma, int tile, int zc, const void *g_in,
                            void *g_out, const void *psi_in, void *psi_out, unsigned *err, cudaStream_t s);
 
+// One box of a batch as the batched kernel sees it (copied to shared memory
+// per work item).  g[k] / psi[k]: the two time levels; cur: which level holds
+// the state at the batch's parity 0.
+struct BatchBox {
+  KParams P;
+  void *g[2];
+  float *psi[2];
+  int op;
+  int cur;
+  int pad[2];
+};
+
+// Persistent single-pass launch over the work items (box, tx | ty << 16, z0, z1)
+// of many boxes; grid = number of thread blocks.  FP32 arithmetic forms only.
+cudaError_t launch_batch_onepass(int precision, int eos, int tile, const BatchBox *boxes, const int4 *items,
+                                 int nitems, int parity, int grid, unsigned *err, cudaStream_t s);
+// Block shape of a tile choice: returns threads per block, sets bx, by.
+int onepass_tile_shape(int tile, int *bx, int *by);
+
 size_t storage_bytes(int precision);  // bytes per stored population
 size_t psi_elem_bytes(int precision);
 
@@ -95,6 +114,9 @@ cudaError_t launch_moments(const KParams &P, int precision, const void *g, const
 cudaError_t launch_diag(const KParams &P, int precision, const void *g, const void *psi,
                         double *partials, double *result, const Launch &L);
 
+// max |u - u_prev| over the box into *out (atomic max; *out must start at 0), u_prev := u.
+cudaError_t launch_max_du(const KParams &P, int precision, const void *g, const void *psi, float *u_prev,
+                          double *out, const Launch &L);
 cudaError_t launch_rho_droplets(const KParams &P, double *rho, const DropletChunk &chunk,
                                 double W, double rho_l, double rho_v, bool first, const Launch &L);
 cudaError_t launch_rho_slab(const KParams &P, double *rho, int axis, double lo, double hi,

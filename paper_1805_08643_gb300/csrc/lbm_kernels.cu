@@ -9,6 +9,8 @@
 //               space (Eq. 4), store f*(x, t) at x into the other buffer.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -176,6 +178,44 @@ __global__ void __launch_bounds__(256) diag_partial_kernel(const typename Types<
   if (threadIdx.x == 0)
 #pragma unroll
     for (int k = 0; k < 5; ++k) partials[blockIdx.x * 5 + k] = red[k][0];
+}
+
+// max over nodes of |u(x) - u_prev(x)| (Eq. 6 velocity, FP64), folded into
+// *out with an atomic max on the bit pattern (non-negative doubles order like
+// their bits); u_prev is overwritten with u in FP32.
+template <int PREC>
+__global__ void __launch_bounds__(256) max_du_kernel(const typename Types<PREC>::S *__restrict__ g,
+                                                     const typename Types<PREC>::Psi *__restrict__ psi,
+                                                     const KParams P, float *__restrict__ u_prev,
+                                                     unsigned long long *__restrict__ out) {
+  double m = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += gridDim.x * blockDim.x) {
+    const int x = i % P.nx, yz = i / P.nx, y = yz % P.ny, z = yz / P.ny;
+    const Nbhd nb(x, y, z, P);
+    double rho, rux, ruy, ruz;
+    node_moments<PREC>(g, psi, P, nb, rho, rux, ruy, ruz);
+    const double u[3] = {rux / rho, ruy / rho, ruz / rho};
+    double d2 = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const double d = u[k] - (double)u_prev[(size_t)k * P.n + i];
+      d2 += d * d;
+      u_prev[(size_t)k * P.n + i] = (float)u[k];
+    }
+    const double d = sqrt(d2);
+    m = (d > m || d != d) ? d : m;
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const double a = red[threadIdx.x], b = red[threadIdx.x + s];
+      red[threadIdx.x] = (b > a || b != b) ? b : a;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(red[0]));
 }
 
 __global__ void diag_final_kernel(const double *__restrict__ partials, int nblocks,
@@ -354,6 +394,15 @@ cudaError_t launch_diag(const KParams &P, int precision, const void *g, const vo
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   diag_final_kernel<<<1, 32, 0, L.stream>>>(partials, kReduceBlocks, result);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_du(const KParams &P, int precision, const void *g, const void *psi, float *u_prev,
+                          double *out, const Launch &L) {
+  const int blocks = (int)std::min<long long>(4 * 152, ((long long)P.n + 255) / 256);
+  LBM_PREC_SWITCH(precision, (max_du_kernel<PR><<<blocks, 256, 0, L.stream>>>(
+                                 (const typename Types<PR>::S *)g, (const typename Types<PR>::Psi *)psi, P, u_prev,
+                                 (unsigned long long *)out)));
   return cudaGetLastError();
 }
 

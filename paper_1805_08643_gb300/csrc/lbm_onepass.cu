@@ -42,29 +42,32 @@ template <int BX, int BY> struct OneSmem {
 // resident CTAs per SM the register budget is sized for
 template <int BX, int BY> constexpr int one_min_blocks() { return (BX + 2) * (BY + 2) <= 256 ? 4 : 2; }
 
+// Operator chosen per thread block at run time (batched boxes of both kinds).
+constexpr int kOpRuntime = 2;
+
+// One x-y tile of one box marched through planes [z0, z1): the whole single
+// pass for those nodes.  OP is kOrth, kNonOrth or kOpRuntime (then op_rt picks).
 template <int PREC, int OP, bool SIGMA, int EOS, int BX, int BY>
-__global__ void __launch_bounds__(((BX + 2) * (BY + 2) + 31) / 32 * 32, (one_min_blocks<BX, BY>()))
-    onepass_kernel(const typename OneTypes<PREC>::S *__restrict__ g_in, typename OneTypes<PREC>::S *__restrict__ g_out,
-                   const float *__restrict__ psi_in, float *__restrict__ psi_out, const KParams P, int zc,
-                   unsigned *__restrict__ err) {
+__device__ __forceinline__ void onepass_tile(const typename OneTypes<PREC>::S *__restrict__ g_in,
+                                             typename OneTypes<PREC>::S *__restrict__ g_out,
+                                             const float *__restrict__ psi_in, float *__restrict__ psi_out,
+                                             const KParams &P, int x0, int y0, int z0, int z1, int op_rt,
+                                             unsigned &e, float *smem) {
   using S = typename OneTypes<PREC>::S;
   using SM = OneSmem<BX, BY>;
   constexpr int EX = SM::EX, NE = SM::NE, PX = SM::PX, NP = SM::NP;
   constexpr int NT = ((BX + 2) * (BY + 2) + 31) / 32 * 32;
-  extern __shared__ float smem[];
   float *sm_f = smem;                  // [2][18][NE]
   float *sm_psi = smem + 2 * 18 * NE;  // [4][NP]
 
   const int tid = threadIdx.x;
   const bool active = tid < NE;
   const int lx = tid % EX, ly = tid / EX;
-  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
   const int nx = P.nx, ny = P.ny, nz = P.nz;
   const unsigned n = (unsigned)P.n, nxy = (unsigned)(nx * ny);
   const int gx = wrap(x0 + lx - 1, nx), gy = wrap(y0 + ly - 1, ny);
   const bool interior = active && lx >= 1 && lx <= BX && ly >= 1 && ly <= BY && x0 + lx - 1 < nx &&
                         y0 + ly - 1 < ny;
-  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, nz);
   const Rates<float> r(P);
   const float rho_ref = P.frho_ref, mG = -P.fG;
 
@@ -127,7 +130,6 @@ __global__ void __launch_bounds__(((BX + 2) * (BY + 2) + 31) / 32 * 32, (one_min
 
   // partial sums of rho(t+1) - rho_ref: A for plane zz-1, B for plane zz
   float A = 0.f, B = 0.f;
-  unsigned e = 0;
   const int c = (ly + 1) * PX + (lx + 1);  // this node in the psi tile
   for (int zz = z0 - 1; zz <= z1; ++zz) {
     float *buf = sm_f + (zz & 1) * 18 * NE;
@@ -159,7 +161,7 @@ __global__ void __launch_bounds__(((BX + 2) * (BY + 2) + 31) / 32 * 32, (one_min
       psi_gradient<float>(p, Sx, Sy, Sz);
       const float k = mG * p[0];
       const float dS4 = SIGMA ? P.fsigma_coef * (Sx * Sx + Sy * Sy + Sz * Sz) : 0.f;
-      if (OP == kNonOrth)
+      if (OP == kNonOrth || (OP == kOpRuntime && op_rt == kNonOrth))
         collide_nonorth<float>(f, rho_ref, k * Sx, k * Sy, k * Sz, dS4, r);
       else
         collide_orth<float>(f, rho_ref, k * Sx, k * Sy, k * Sz, dS4, r);
@@ -197,6 +199,45 @@ __global__ void __launch_bounds__(((BX + 2) * (BY + 2) + 31) / 32 * 32, (one_min
       A = B + s_in;
       B = s_up;
     }
+  }
+}
+
+template <int PREC, int OP, bool SIGMA, int EOS, int BX, int BY>
+__global__ void __launch_bounds__(((BX + 2) * (BY + 2) + 31) / 32 * 32, (one_min_blocks<BX, BY>()))
+    onepass_kernel(const typename OneTypes<PREC>::S *__restrict__ g_in, typename OneTypes<PREC>::S *__restrict__ g_out,
+                   const float *__restrict__ psi_in, float *__restrict__ psi_out, const KParams P, int zc,
+                   unsigned *__restrict__ err) {
+  extern __shared__ float smem[];
+  unsigned e = 0;
+  const int z0 = blockIdx.z * zc;
+  onepass_tile<PREC, OP, SIGMA, EOS, BX, BY>(g_in, g_out, psi_in, psi_out, P, blockIdx.x * BX, blockIdx.y * BY, z0,
+                                             min(z0 + zc, P.nz), OP, e, smem);
+  if (e) atomicOr(err, e);
+}
+
+// Many boxes in one persistent launch: thread block b takes work items b,
+// b + gridDim.x, ...; an item is one tile of one box and a range of planes.
+template <int PREC, int EOS, int BX, int BY>
+__global__ void __launch_bounds__(((BX + 2) * (BY + 2) + 31) / 32 * 32, (one_min_blocks<BX, BY>()))
+    batch_onepass_kernel(const BatchBox *__restrict__ boxes, const int4 *__restrict__ items, int nitems, int parity,
+                         unsigned *__restrict__ err) {
+  using S = typename OneTypes<PREC>::S;
+  extern __shared__ float smem[];
+  __shared__ BatchBox bb;
+  unsigned e = 0;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 w = items[it];  // (box, tx | ty << 16, z0, z1)
+    __syncthreads();           // every thread is done with the previous item's descriptor
+    {
+      const int *src = (const int *)(boxes + w.x);
+      int *dst = (int *)&bb;
+      for (int k = threadIdx.x; k < (int)(sizeof(BatchBox) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    const int in = bb.cur ^ parity;
+    onepass_tile<PREC, kOpRuntime, true, EOS, BX, BY>(
+        (const S *)bb.g[in], (S *)bb.g[in ^ 1], bb.psi[in], bb.psi[in ^ 1], bb.P, (w.y & 0xffff) * BX,
+        (w.y >> 16) * BY, w.z, w.w, bb.op, e, smem);
   }
   if (e) atomicOr(err, e);
 }
@@ -251,7 +292,58 @@ cudaError_t by_op(const KParams &P, int op, bool sigma, int tile, const void *g_
                : by_eos<PREC, kOrth, false>(P, tile, g_in, g_out, psi_in, psi_out, zc, err, s);
 }
 
+template <int PREC, int EOS, int BX, int BY>
+cudaError_t batch_tile(const BatchBox *boxes, const int4 *items, int nitems, int parity, int grid, unsigned *err,
+                       cudaStream_t s) {
+  constexpr int NT = ((BX + 2) * (BY + 2) + 31) / 32 * 32;
+  constexpr size_t smem = OneSmem<BX, BY>::bytes;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(batch_onepass_kernel<PREC, EOS, BX, BY>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  batch_onepass_kernel<PREC, EOS, BX, BY><<<grid, NT, smem, s>>>(boxes, items, nitems, parity, err);
+  return cudaGetLastError();
+}
+
+template <int PREC, int EOS>
+cudaError_t batch_by_tile(int tile, const BatchBox *boxes, const int4 *items, int nitems, int parity, int grid,
+                          unsigned *err, cudaStream_t s) {
+  switch (tile) {
+    case kTile32x4: return batch_tile<PREC, EOS, 32, 4>(boxes, items, nitems, parity, grid, err, s);
+    case kTile64x4: return batch_tile<PREC, EOS, 64, 4>(boxes, items, nitems, parity, grid, err, s);
+    default: return batch_tile<PREC, EOS, 32, 8>(boxes, items, nitems, parity, grid, err, s);
+  }
+}
+
 }  // namespace
+
+int onepass_tile_shape(int tile, int *bx, int *by) {
+  *bx = tile == kTile64x4 ? 64 : 32;
+  *by = tile == kTile32x8 ? 8 : 4;
+  return ((*bx + 2) * (*by + 2) + 31) / 32 * 32;
+}
+
+cudaError_t launch_batch_onepass(int precision, int eos, int tile, const BatchBox *boxes, const int4 *items,
+                                 int nitems, int parity, int grid, unsigned *err, cudaStream_t s) {
+  if (precision == kF32) {
+    switch (eos) {
+      case kEosCS: return batch_by_tile<kF32, kEosCS>(tile, boxes, items, nitems, parity, grid, err, s);
+      case kEosExp: return batch_by_tile<kF32, kEosExp>(tile, boxes, items, nitems, parity, grid, err, s);
+      default: return batch_by_tile<kF32, kEosNone>(tile, boxes, items, nitems, parity, grid, err, s);
+    }
+  }
+  if (precision == kF16) {
+    switch (eos) {
+      case kEosCS: return batch_by_tile<kF16, kEosCS>(tile, boxes, items, nitems, parity, grid, err, s);
+      case kEosExp: return batch_by_tile<kF16, kEosExp>(tile, boxes, items, nitems, parity, grid, err, s);
+      default: return batch_by_tile<kF16, kEosNone>(tile, boxes, items, nitems, parity, grid, err, s);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_onepass(const KParams &P, int precision, int op, bool sigma, int tile, int zc, const void *g_in,
                            void *g_out, const void *psi_in, void *psi_out, unsigned *err, cudaStream_t s) {

@@ -61,6 +61,23 @@ SIGNATURES = {
     "lbm_get_tuning": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "lbm_step_count": (ctypes.c_longlong, [_vp]),
     "lbm_step_static": (_c_int, [_vp, _vp, _vp]),
+    "lbm_batch_box_bytes": (ctypes.c_size_t, [_c_int, ctypes.POINTER(ctypes.c_int * 3)]),
+    "lbm_batch_create": (_c_int, [_c_int, _c_int, ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
+    "lbm_batch_add": (_c_int, [_vp, ctypes.POINTER(ctypes.c_int * 3), ctypes.POINTER(LbmEos), _c_double,
+                               ctypes.POINTER(LbmRates), _c_int, _c_double, ctypes.POINTER(_c_int)]),
+    "lbm_batch_remove": (_c_int, [_vp, _c_int]),
+    "lbm_batch_init_droplet": (_c_int, [_vp, _c_int, _dp, _c_double, _c_double, _c_double, _c_double]),
+    "lbm_batch_init_flat": (_c_int, [_vp, _c_int, _c_int, _c_double, _c_double, _c_double, _c_double, _c_double]),
+    "lbm_batch_set_tuning": (_c_int, [_vp, _c_int, _c_int, _c_int]),
+    "lbm_batch_step": (_c_int, [_vp, _c_int]),
+    "lbm_batch_moments": (_c_int, [_vp, _c_int, _vp, _vp, _c_int]),
+    "lbm_batch_diag": (_c_int, [_vp, _c_int, _dp]),
+    "lbm_batch_max_du": (_c_int, [_vp, _c_int, ctypes.POINTER(_c_int), _dp]),
+    "lbm_batch_check": (_c_int, [_vp]),
+    "lbm_batch_info": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), _szp]),
+    "lbm_batch_box_steps": (ctypes.c_longlong, [_vp, _c_int]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "lbm_batch_destroy": (None, [_vp]),
     "lbm_destroy": (None, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
     "lbm_status_string": (ctypes.c_char_p, [_c_int]),
@@ -256,3 +273,107 @@ class Lattice:
                                          ctypes.byref(nf)), "lbm_kernel_times")
         return {"psi_ms": mp.value, "psi_launches": npsi.value, "fused_ms": mf.value,
                 "fused_launches": nf.value}
+
+
+class Batch:
+    """Many boxes advanced together (include/lbm.h, "batches"); FP32 arithmetic."""
+
+    def __init__(self, precision="f32", eos="cs", hbm_budget_bytes=1 << 40, stream=None):
+        import torch
+
+        self.precision = precision
+        self.eos = eos
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = lib.lbm_batch_create(PRECISIONS[precision], EOS_KINDS[eos], int(hbm_budget_bytes),
+                                  ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h))
+        if st != OK:
+            raise LBMError(st, "lbm_batch_create")
+        self._h = h
+        self.grids = {}
+
+    def _check(self, st, where):
+        if st != OK:
+            raise LBMError(st, where, lib.lbm_batch_last_error(self._h).decode())
+
+    @staticmethod
+    def box_bytes(precision, grid):
+        return lib.lbm_batch_box_bytes(PRECISIONS[precision], ctypes.byref((ctypes.c_int * 3)(*grid)))
+
+    def add(self, grid, operator="nonorth", a=1.0, b=4.0, R=1.0, T=0.0, psi0=1.0, rho0=1.0, G=-1.0,
+            rates: Rates | None = None, sigma=0.0):
+        rates = rates or Rates()
+        g = (ctypes.c_int * 3)(*grid)
+        e = LbmEos(EOS_KINDS[self.eos], a, b, R, T, psi0, rho0)
+        r = LbmRates(rates.s_e, rates.s_nu, rates.s_q, rates.s_pi, rates.s_eps, rates.s_m)
+        i = ctypes.c_int()
+        self._check(lib.lbm_batch_add(self._h, ctypes.byref(g), ctypes.byref(e), G, ctypes.byref(r),
+                                      OPERATORS[operator], sigma, ctypes.byref(i)), "lbm_batch_add")
+        self.grids[i.value] = tuple(grid)
+        return i.value
+
+    def try_add(self, *args, **kw):
+        """add(), or None when the HBM budget has no room."""
+        try:
+            return self.add(*args, **kw)
+        except LBMError as e:
+            if e.status == ERR_OOM:
+                return None
+            raise
+
+    def remove(self, box):
+        self._check(lib.lbm_batch_remove(self._h, box), "lbm_batch_remove")
+        self.grids.pop(box, None)
+
+    def init_droplet(self, box, centre, R, W, rho_l, rho_v):
+        c = (ctypes.c_double * 3)(*centre)
+        self._check(lib.lbm_batch_init_droplet(self._h, box, c, R, W, rho_l, rho_v), "lbm_batch_init_droplet")
+
+    def init_flat(self, box, axis, lo, hi, W, rho_l, rho_v):
+        self._check(lib.lbm_batch_init_flat(self._h, box, axis, lo, hi, W, rho_l, rho_v), "lbm_batch_init_flat")
+
+    def set_tuning(self, tile=1, box=-1, z_planes=0):
+        self._check(lib.lbm_batch_set_tuning(self._h, tile, box, z_planes), "lbm_batch_set_tuning")
+
+    def step(self, n=1):
+        self._check(lib.lbm_batch_step(self._h, int(n)), "lbm_batch_step")
+
+    def moments(self, box):
+        nx, ny, nz = self.grids[box]
+        n = nx * ny * nz
+        rho, u = np.empty(n), np.empty(3 * n)
+        self._check(lib.lbm_batch_moments(self._h, box, _ptr(rho), _ptr(u), 0), "lbm_batch_moments")
+        return rho.reshape(nz, ny, nx), u.reshape(3, nz, ny, nx)
+
+    def diag(self, box):
+        out = (ctypes.c_double * 5)()
+        self._check(lib.lbm_batch_diag(self._h, box, out), "lbm_batch_diag")
+        return {"mass": out[0], "momentum": (out[1], out[2], out[3]), "max_u": out[4]}
+
+    def max_du(self, boxes):
+        ids = (ctypes.c_int * len(boxes))(*boxes)
+        out = (ctypes.c_double * max(len(boxes), 1))()
+        self._check(lib.lbm_batch_max_du(self._h, len(boxes), ids, out), "lbm_batch_max_du")
+        return [out[k] for k in range(len(boxes))]
+
+    def check(self):
+        return lib.lbm_batch_check(self._h)
+
+    def info(self):
+        lb, wi, by = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        self._check(lib.lbm_batch_info(self._h, ctypes.byref(lb), ctypes.byref(wi), ctypes.byref(by)), "lbm_batch_info")
+        return {"live_boxes": lb.value, "work_items": wi.value, "bytes_used": by.value}
+
+    def box_steps(self, box):
+        return lib.lbm_batch_box_steps(self._h, box)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.lbm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
