@@ -246,6 +246,47 @@ def e2e_run(op, prec, edge, steps):
     return t1 - t0, 8 * n, 32 * n
 
 
+def batched_run(steps, warmup, n_boxes=512):
+    """The batched workload: n_boxes periodic boxes (edges 32/48/64/96), one launch per step."""
+    import torch
+
+    from paper_1805_08643_gb300 import synth, thermo, tune
+    from paper_1805_08643_gb300.lbm import Batch, Rates
+
+    specs = synth.batched_boxes(n_boxes)
+    a = 0.25  # stable over T/T_c in [0.6, 0.9] with W = 5 and sigma = 0.105
+    Tc = thermo.critical_temperature(a, B, R_GAS)
+    batch = Batch("f32", "cs", hbm_budget_bytes=200 << 30)
+    nodes = 0
+    for k, sp in enumerate(specs):
+        rl, rv = thermo.coexistence_cs(sp.T_over_Tc, a, B, R_GAS)
+        box = batch.add((sp.edge,) * 3, "nonorth" if k % 2 == 0 else "orth", a=a, b=B, R=R_GAS,
+                        T=sp.T_over_Tc * Tc, G=G, rates=Rates(**RATES), sigma=SIGMA_DROPLET)
+        batch.init_droplet(box, (sp.edge / 2,) * 3, sp.radius, W_DROPLET, rl, rv)
+        nodes += sp.edge ** 3
+    tile, zc, table = tune.tune_batch(batch)
+    steps += steps % 2
+    batch.step(max(2, warmup + warmup % 2))
+    stream = batch.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    stream.synchronize()
+    e0.record(stream)
+    batch.step(steps)
+    e1.record(stream)
+    stream.synchronize()
+    ms = e0.elapsed_time(e1)
+    status = batch.check()
+    info = batch.info()
+    batch.close()
+    return {"mlups": nodes * steps / (ms / 1e3) / 1e6, "ms_per_step": ms / steps, "boxes": n_boxes, "nodes": nodes,
+            "work_items": info["work_items"], "tile": tune.TILES[tile], "z_planes": zc,
+            "step_gbs": (2 * 19 * 4 + 8) * nodes / (ms / steps / 1e3) / 1e9,
+            "tuning_ms_per_step": {f"{tune.TILES[t]}/z{z}": round(v, 3) for (t, z), v in table.items()},
+            "operators": "alternating non-orthogonal / orthogonal", "status": status,
+            "physics": "a=0.25, W=5, sigma=0.105, T/Tc~U[0.6,0.9], R~U[6,edge/3], FP32"}
+
+
 def cpu_baseline(seconds_target=15.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload."""
     from oracle import lbm_oracle as L
@@ -391,6 +432,9 @@ def main():
                                              "fused_ms": f_fused,
                                              "hbm_frac_fused": FUSED_BYTES[fprec] * n / (f_fused / 1e3) / 1e9 / hbm_peak,
                                              "status": fst}
+
+    if args.forms == "all":
+        forms["batched_512"] = batched_run(args.steps, args.warmup)
 
     e2e = None
     if not args.no_e2e:

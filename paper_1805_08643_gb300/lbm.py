@@ -283,7 +283,8 @@ class Batch:
 
         self.precision = precision
         self.eos = eos
-        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        # graphs cannot be captured on the legacy default stream: a batch gets its own
+        self._stream = stream if stream is not None else torch.cuda.Stream()
         h = ctypes.c_void_p()
         st = lib.lbm_batch_create(PRECISIONS[precision], EOS_KINDS[eos], int(hbm_budget_bytes),
                                   ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h))
@@ -295,6 +296,11 @@ class Batch:
     def _check(self, st, where):
         if st != OK:
             raise LBMError(st, where, lib.lbm_batch_last_error(self._h).decode())
+
+    @property
+    def stream(self):
+        """The torch.cuda.Stream the batch's work runs on."""
+        return self._stream
 
     @staticmethod
     def box_bytes(precision, grid):
