@@ -287,6 +287,25 @@ def batched_run(steps, warmup, n_boxes=512):
             "physics": "a=0.25, W=5, sigma=0.105, T/Tc~U[0.6,0.9], R~U[6,edge/3], FP32"}
 
 
+def served_run(n_jobs=24, load=1.0, max_steps=2000, tol=1e-7):
+    """The served workload, scaled down: Poisson droplet / slab jobs, edges U[48, 96], continuous batching."""
+    from paper_1805_08643_gb300 import synth
+    from paper_1805_08643_gb300.serve import BatchBackend, Server
+
+    # offered load relative to a capacity estimate: GPU rate 20 GLUPS over jobs of mean edge^3 x max_steps
+    mean_nodes = (96 ** 4 - 48 ** 4) / (4 * 48)
+    capacity = 20e9 / (mean_nodes * max_steps)
+    jobs = synth.job_stream(n_jobs, rate_per_s=load * capacity, edge_lo=48, edge_hi=96)
+    be = BatchBackend("f32", hbm_budget_bytes=64 << 30)
+    rep = Server(be, check_every=100, tol=tol, max_steps=max_steps, min_steps=200).run(jobs)
+    be.close()
+    out = rep.summary()
+    out.update({"offered_jobs_per_s": load * capacity, "tol_max_du_per_100_steps": tol, "max_steps": max_steps,
+                "workload": f"{n_jobs} jobs, edge U[48,96], droplet or slab, T/Tc U[0.6,0.9], "
+                            "operator random, FP32, a=0.25, W=5"})
+    return out
+
+
 def cpu_baseline(seconds_target=15.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload."""
     from oracle import lbm_oracle as L
@@ -435,6 +454,7 @@ def main():
 
     if args.forms == "all":
         forms["batched_512"] = batched_run(args.steps, args.warmup)
+        forms["served"] = served_run()
 
     e2e = None
     if not args.no_e2e:
