@@ -306,6 +306,70 @@ def served_run(n_jobs=24, load=1.0, max_steps=2000, tol=1e-7):
     return out
 
 
+def precision_study(edge=512, steps=5000):
+    """FP32 and FP16-storage forms against the FP64 form on the 27-droplet workload.
+
+    512^3 box, 27 droplets on a jittered 3x3x3 lattice (R ~ U[12, 40], seed 1805),
+    T = 0.6 T_c, a = 0.25 (a = 1 is unstable here), W = 5, sigma = 0.105, s_nu = 1.0,
+    other rates 1.1, non-orthogonal operator.  Per form: density ratio (mean of the
+    droplet-centre densities over the vapour median), Laplace Delta p of each droplet
+    and the maximum spurious |u|, with errors relative to the FP64 run.
+    """
+    import torch
+
+    from paper_1805_08643_gb300 import synth, thermo
+    from paper_1805_08643_gb300.lbm import Lattice, Rates
+
+    a = 0.25
+    Tc = thermo.critical_temperature(a, B, R_GAS)
+    T = 0.6 * Tc
+    rl, rv = thermo.coexistence_cs(0.6, a, B, R_GAS)
+    centres, radii = synth.random_droplets(box=edge)
+
+    def p_eos(r):
+        e = B * r / 4
+        return r * R_GAS * T * (1 + e + e * e - e ** 3) / (1 - e) ** 3 - a * r * r
+
+    out = {}
+    for prec in ("f64", "f32", "f16"):
+        lat = Lattice((edge,) * 3, operator="nonorth", precision=prec, a=a, T=T, G=G, rates=Rates(**RATES),
+                      sigma=SIGMA_DROPLET)
+        lat.init_droplets(centres, radii, W_DROPLET, rl, rv)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.step(steps)
+        status = lat.check()
+        t1 = time.perf_counter()
+        rho, u = lat.moments()
+        diag = lat.diag()
+        lat.close()
+        del lat
+        torch.cuda.empty_cache()
+        idx = np.rint(centres).astype(int) % edge
+        rho_in = rho[idx[:, 2], idx[:, 1], idx[:, 0]]
+        vap = rho[rho < 0.5 * (rl + rv)]
+        rho_out = float(np.median(vap))
+        umag = np.sqrt((u * u).sum(0))
+        out[prec] = {"rho_in": rho_in, "rho_out": rho_out, "dp": p_eos(rho_in) - p_eos(rho_out),
+                     "umax": float(umag.max()), "mass": diag["mass"], "seconds": t1 - t0,
+                     "mlups": edge ** 3 * steps / (t1 - t0) / 1e6, "status": status}
+        del rho, u, umag, vap
+    ref = out["f64"]
+    table = {}
+    for prec, r in out.items():
+        ratio = float(np.mean(r["rho_in"]) / r["rho_out"])
+        ratio_ref = float(np.mean(ref["rho_in"]) / ref["rho_out"])
+        dp_err = np.abs(r["dp"] - ref["dp"]) / np.abs(ref["dp"])
+        table[prec] = {"density_ratio": ratio, "density_ratio_rel_err": abs(ratio / ratio_ref - 1),
+                       "laplace_dp_rel_err_max": float(dp_err.max()), "laplace_dp_rel_err_mean": float(dp_err.mean()),
+                       "max_spurious_u": r["umax"], "max_spurious_u_abs_err": abs(r["umax"] - ref["umax"]),
+                       "rel_mass_vs_fp64": r["mass"] / ref["mass"] - 1, "seconds": r["seconds"],
+                       "mlups": r["mlups"], "status": r["status"]}
+    return {"study": "precision", "edge": edge, "steps": steps, "droplets": len(radii),
+            "physics": "T=0.6Tc, a=0.25, W=5, sigma=0.105, s_nu=1.0, other rates 1.1, non-orthogonal",
+            "forms": table}
+
+
 def cpu_baseline(seconds_target=15.0):
     """The FP64 oracle, as it stands, on a bounded sample of the workload."""
     from oracle import lbm_oracle as L
@@ -381,6 +445,9 @@ def main():
     ap.add_argument("--forms", default="all", help="'all' or 'headline'")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--study", default=None, choices=["precision"],
+                    help="run a study instead of the benchmark line (minutes)")
+    ap.add_argument("--study-steps", type=int, default=5000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -395,6 +462,10 @@ def main():
 
     build()
     torch.cuda.set_device(local)
+    if args.study == "precision":
+        if rank == 0:
+            print(json.dumps(precision_study(args.edge if args.edge != EDGE else 512, args.study_steps)))
+        return
     n = args.edge ** 3
     hbm_peak, peak_kind = peaks()
 
