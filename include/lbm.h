@@ -157,12 +157,15 @@ lbm_status lbm_set_profiling(lbm_ctx *ctx, int enabled);
 lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
                             double *ms_fused, long long *n_fused);
 
-/* Kernel choice for this context.  single_pass = 1 (LBM_F32 and
- * LBM_F32_STORE_F16 only) runs each step as one kernel that also produces psi
- * of the next step, recomputing collisions on a one-node ring around each
- * thread block's tile; 0 (the default) runs the psi pass and the fused pass.  tile picks the x-y tile of the single-pass kernel (0: 32x4, 1: 32x8,
- * 2: 64x4); z_planes the z planes each thread block marches through (0 =
- * automatic).  Results do not depend on tile or z_planes.  Errors: LBM_ERR_ARG. */
+/* Kernel choice for this context.  single_pass = 0 (the default) runs the psi
+ * pass and the fused pass.  1 (LBM_F32 and LBM_F32_STORE_F16 only) runs each
+ * step as one kernel that also produces psi of the next step, recomputing
+ * collisions on a one-node ring around each thread block's tile.  2 runs that
+ * single pass with its data moved by bulk asynchronous copies (LBM_F32 only,
+ * Nx a multiple of 4 and at least 40; 32x8 tiles).  tile picks the x-y tile of
+ * the single-pass kernel (0: 32x4, 1: 32x8, 2: 64x4); z_planes the z planes
+ * each thread block marches through (0 = automatic).  Results do not depend on
+ * tile or z_planes.  Errors: LBM_ERR_ARG. */
 lbm_status lbm_set_tuning(lbm_ctx *ctx, int single_pass, int tile, int z_planes);
 lbm_status lbm_get_tuning(const lbm_ctx *ctx, int *single_pass, int *tile, int *z_planes);
 

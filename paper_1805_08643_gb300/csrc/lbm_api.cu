@@ -31,6 +31,7 @@ struct lbm_ctx {
   int pc = 0;               // which level holds psi of the current state
   void *scratch = nullptr;
   bool onepass = false;     // single-pass kernel (FP32 arithmetic forms)
+  bool onepass_tma = false; // ... in its bulk-copy variant
   int tile = 1, zc = 0;     // its tile shape and z planes per CTA (0 = automatic)
   bool owns = false, have_buffers = false, initialized = false, psi_valid = false;
   long long steps = 0;
@@ -285,6 +286,7 @@ lbm_status lbm_check(lbm_ctx *c) {
   CK(cudaMemcpyAsync(&w, err_word(c), sizeof(unsigned), cudaMemcpyDeviceToHost, c->L.stream), "read error word");
   CK(cudaMemsetAsync(err_word(c), 0, sizeof(unsigned), c->L.stream), "clear error word");
   CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
+  if (w & lbm::kErrTimeout) return fail(c, LBM_ERR_TIMEOUT, "a bounded wait for asynchronous copies gave up");
   if (w & lbm::kErrNonFinite) return fail(c, LBM_ERR_NONFINITE, "non-finite density");
   if (w & lbm::kErrEosDomain) return fail(c, LBM_ERR_EOS_DOMAIN, "density left the domain of the EOS");
   return LBM_OK;
@@ -307,8 +309,10 @@ lbm_status lbm_step(lbm_ctx *c, int n) {
     if (c->onepass) {
       void *pin = cur_psi(c), *pout = psi_at(c, c->pc ^ 1);
       CK(timed(c, 1, [&] {
-           return lbm::launch_onepass(c->P, c->precision, c->op, c->sigma_on, c->tile, zc, gin, gout, pin, pout,
-                                      err_word(c), c->L.stream);
+           return c->onepass_tma ? lbm::launch_onepass_tma(c->P, c->precision, c->op, c->sigma_on, zc, gin, gout,
+                                                           pin, pout, err_word(c), c->L.stream)
+                                 : lbm::launch_onepass(c->P, c->precision, c->op, c->sigma_on, c->tile, zc, gin,
+                                                       gout, pin, pout, err_word(c), c->L.stream);
          }),
          "single-pass kernel");
       c->pc ^= 1;
@@ -434,10 +438,15 @@ lbm_status lbm_kernel_times(lbm_ctx *c, double *ms_psi, long long *n_psi, double
 }
 
 lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
-  if (!c || tile < 0 || tile > 2 || z_planes < 0) return fail(c, LBM_ERR_ARG, "bad tuning");
+  if (!c || single_pass < 0 || single_pass > 2 || tile < 0 || tile > 2 || z_planes < 0)
+    return fail(c, LBM_ERR_ARG, "bad tuning");
   if (single_pass && c->precision == LBM_F64) return fail(c, LBM_ERR_ARG, "single pass needs FP32 arithmetic");
+  if (single_pass == 2 && !lbm::onepass_tma_supported(c->P, c->precision))
+    return fail(c, LBM_ERR_ARG, "bulk-copy single pass needs FP32 storage, Nx % 4 == 0 and Nx >= 40");
   if (c->onepass != (single_pass != 0)) c->psi_valid = false;
   c->onepass = single_pass != 0;
+  c->onepass_tma = single_pass == 2;
+  if (c->onepass_tma) tile = lbm::kTile32x8;
   c->tile = tile;
   c->zc = z_planes;
   return LBM_OK;
@@ -445,7 +454,7 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
 
 lbm_status lbm_get_tuning(const lbm_ctx *c, int *single_pass, int *tile, int *z_planes) {
   if (!c) return LBM_ERR_ARG;
-  if (single_pass) *single_pass = c->onepass ? 1 : 0;
+  if (single_pass) *single_pass = c->onepass ? (c->onepass_tma ? 2 : 1) : 0;
   if (tile) *tile = c->tile;
   if (z_planes) *z_planes = c->zc > 0 ? c->zc : auto_zc(c);
   return LBM_OK;

@@ -12,7 +12,7 @@ enum Operator { kOrth = 0, kNonOrth = 1 };
 enum EosKind { kEosCS = 0, kEosExp = 1, kEosNone = 2 };
 
 // Error bits the kernels set in the device error word.
-enum : unsigned { kErrEosDomain = 1u, kErrNonFinite = 2u };
+enum : unsigned { kErrEosDomain = 1u, kErrNonFinite = 2u, kErrTimeout = 4u };
 
 // Everything a kernel needs about the box and the physics, passed by value.
 struct KParams {
@@ -99,6 +99,12 @@ cudaError_t launch_batch_onepass(int precision, int eos, int tile, const BatchBo
                                  int nitems, int parity, int grid, unsigned *err, cudaStream_t s);
 // Block shape of a tile choice: returns threads per block, sets bx, by.
 int onepass_tile_shape(int tile, int *bx, int *by);
+
+// Single-pass step whose data movement runs on bulk asynchronous copies
+// (FP32 storage, 32x8 tiles, nx % 4 == 0 and nx >= 40).
+bool onepass_tma_supported(const KParams &P, int precision);
+cudaError_t launch_onepass_tma(const KParams &P, int precision, int op, bool sigma, int zc, const void *g_in,
+                               void *g_out, const void *psi_in, void *psi_out, unsigned *err, cudaStream_t s);
 
 size_t storage_bytes(int precision);  // bytes per stored population
 size_t psi_elem_bytes(int precision);

@@ -94,3 +94,52 @@ def test_single_pass_matches_two_pass_fp32():
     a = _run((32, 32, 32), "nonorth", "f32", 100, single_pass=True)
     b = _run((32, 32, 32), "nonorth", "f32", 100, single_pass=False)
     assert max_abs(a[0], b[0]) < 1e-6 and max_abs(a[1], b[1]) < 1e-6
+
+
+@pytest.mark.parametrize("grid", [(40, 36, 30), (48, 40, 36), (72, 24, 20)])
+@pytest.mark.parametrize("op", OPS)
+def test_bulk_copy_single_pass_matches_register_single_pass(grid, op):
+    """The bulk-copy kernel computes what the register-prefetch kernel computes."""
+    phys = physics()
+    rl, rv = coexistence(0.8)
+    out = {}
+    for mode in (True, "tma"):
+        for zc in (0, 7):
+            lat = lattice(grid, op, "f32", phys)
+            lat.set_tuning(mode, 1, zc)
+            lat.init_droplet(tuple(n / 2 for n in grid), 8.0, 2.0, rl, rv)
+            lat.step(30)
+            assert lat.check() == 0
+            out[(mode, zc)] = lat.moments()
+            lat.close()
+    ref = out[(True, 0)]
+    for k, (rho, u) in out.items():
+        assert max_abs(rho, ref[0]) <= 1e-6 and max_abs(u, ref[1]) <= 1e-6, k
+
+
+def test_bulk_copy_single_pass_against_fp64_oracle(oracle_runs):
+    grid = (40, 32, 32)
+    rho_o, u_o = oracle_runs(grid, "nonorth")
+    phys = physics(T_over_Tc=0.8)
+    rl, rv = coexistence(0.8)
+    lat = lattice(grid, "nonorth", "f32", phys)
+    lat.set_tuning("tma", 1, 0)
+    lat.init_droplet(tuple(n / 2 for n in grid), 8.0, 2.0, rl, rv)
+    lat.step(200)
+    assert lat.check() == 0
+    rho, u = lat.moments()
+    lat.close()
+    assert max_abs(rho, rho_o) <= TOL["f32"] and max_abs(u, u_o) <= TOL["f32"]
+
+
+def test_bulk_copy_mode_rejects_unsupported_boxes():
+    from paper_1805_08643_gb300.lbm import LBMError
+
+    lat = lattice((36, 32, 32), "nonorth", "f32", physics())
+    with pytest.raises(LBMError, match="ERR_ARG"):
+        lat.set_tuning("tma")  # Nx < 40
+    lat.close()
+    lat = lattice((64, 32, 32), "nonorth", "f16", physics())
+    with pytest.raises(LBMError, match="ERR_ARG"):
+        lat.set_tuning("tma")  # FP32 storage only
+    lat.close()
