@@ -1,0 +1,73 @@
+"""Parity at the benchmark's full size (256^3) on sampled nodes, and the largest box.
+
+The oracle cannot run 256^3, but one step of one node depends only on the
+populations within three nodes of it: the GPU state f(t) is downloaded, the
+7^3 neighbourhood of each sampled node is stepped by the oracle as a periodic
+box, and the oracle's rho(t+1), u(t+1) and f(t+1) at the centre are compared
+with the GPU's (same launch configuration as bench.py: two-pass step).
+"""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import coexistence, lattice, physics
+from oracle import lbm_oracle as L
+
+pytestmark = pytest.mark.gpu
+
+EDGE = 256
+
+
+def _samples(rng, n, count):
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (n // 2, n // 2, n // 2), (n // 2 + 40, n // 2, n // 2),
+           (n // 2, n // 2 - 38, n // 2 + 3), (0, n // 2, n - 1)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(count - len(pts))]
+    return pts
+
+
+def _cube(f, x, y, z, n):
+    iz, iy, ix = [(np.arange(c - 3, c + 4) % n) for c in (z, y, x)]
+    return f[np.ix_(np.arange(19), iz, iy, ix)]
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 5e-6)])
+@pytest.mark.parametrize("op", ["nonorth", "orth"])
+def test_sampled_one_step_parity_at_256(op, prec, tol):
+    phys = physics(T_over_Tc=0.7, sigma=0.105)
+    rl, rv = coexistence(0.7)
+    lat = lattice((EDGE,) * 3, op, prec, phys)
+    lat.init_droplet((EDGE / 2,) * 3, 40.0, 5.0, rl, rv)
+    lat.step(20)
+    f_t = lat.populations()
+    lat.step(1)
+    f_t1 = lat.populations()
+    rho, u = lat.moments()
+    assert lat.check() == 0
+    lat.close()
+    p = L.Params(grid=(7, 7, 7), operator=op, **phys)
+    rng = np.random.default_rng(1805)
+    worst = 0.0
+    for (x, y, z) in _samples(rng, EDGE, 48):
+        cube = _cube(f_t, x, y, z, EDGE)
+        nxt = L.step(p, cube)
+        r_o, u_o, _, _ = L.macroscopic(p, nxt)
+        err = max(abs(r_o[3, 3, 3] - rho[z, y, x]), float(np.max(np.abs(u_o[:, 3, 3, 3] - u[:, z, y, x]))),
+                  float(np.max(np.abs(nxt[:, 3, 3, 3] - f_t1[:, z, y, x]))))
+        worst = max(worst, err)
+        assert err <= tol, ((x, y, z), err)
+    print(f"{op} {prec} 256^3 sampled one-step parity: worst {worst:.2e}")
+
+
+def test_largest_box_512_fp64_conserves_mass():
+    n = 512
+    phys = physics(T_over_Tc=0.7, sigma=0.105)
+    rl, rv = coexistence(0.7)
+    lat = lattice((n,) * 3, "nonorth", "f64", phys)
+    lat.init_droplet((n / 2,) * 3, 80.0, 5.0, rl, rv)
+    d0 = lat.diag()
+    lat.step(4)
+    d1 = lat.diag()
+    assert lat.check() == 0
+    lat.close()
+    assert abs(d1["mass"] / d0["mass"] - 1) < 1e-13
+    assert max(abs(m) for m in d1["momentum"]) < 1e-12 * d0["mass"]
