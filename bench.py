@@ -182,13 +182,16 @@ def make_lattice(op, prec, edge, sigma=SIGMA_DROPLET):
     return lat, rl, rv
 
 
-def time_form(op, prec, edge, steps, warmup, world, clocks_index=None, field="droplet", single_pass=False):
+def time_form(op, prec, edge, steps, warmup, world, clocks_index=None, field="droplet", single_pass=False,
+              eos_arith="f64"):
     """Device-timed steps of one form; returns (ms_per_step, kernel times, clocks)."""
     import torch
 
     lat, rl, rv = make_lattice(op, prec, edge, SIGMA_DROPLET if field == "droplet" else SIGMA_FLAT)
     if single_pass:
         lat.set_tuning(True, 1, 0)
+    if eos_arith != "f64":
+        lat.set_eos_arith(eos_arith)
     if field == "droplet":
         lat.init_droplet((edge / 2,) * 3, 40.0 * edge / 256, W_DROPLET, rl, rv)
     else:
@@ -514,6 +517,15 @@ def main():
                     "status": fst,
                 }
 
+        for fprec in ("f32", "f16"):
+            fms, fkt, _, fst = time_form("nonorth", fprec, args.edge, args.steps, args.warmup, world,
+                                         eos_arith="f32x2")
+            f_fused = fkt["fused_ms"] / max(fkt["fused_launches"], 1)
+            f_psi = fkt["psi_ms"] / max(fkt["psi_launches"], 1)
+            forms[f"nonorth_{fprec}_droplet_eos_f32x2"] = {
+                "mlups": n * args.steps / (fms / 1e3) / 1e6, "ms_per_step": fms / args.steps, "fused_ms": f_fused,
+                "psi_ms": f_psi, "psi_gbs": PSI_BYTES[fprec] * n / (f_psi / 1e3) / 1e9, "status": fst,
+                "note": "EOS radicand in compensated FP32 pairs instead of FP64"}
         for fprec in ("f64", "f32"):
             steps_f = max(10, args.steps // (8 if fprec == "f64" else 1))
             fms, fkt, _, fst = time_form("nonorth", fprec, args.edge, steps_f, args.warmup, world, field="flat")

@@ -167,6 +167,12 @@ lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
  * each thread block marches through (0 = automatic).  Results do not depend on
  * tile or z_planes.  Errors: LBM_ERR_ARG. */
 lbm_status lbm_set_tuning(lbm_ctx *ctx, int single_pass, int tile, int z_planes);
+
+/* Arithmetic of the EOS radicand in the psi pass of the FP32-arithmetic forms:
+ * 0 (the default) FP64; 1 compensated FP32 pairs (error-free transformations,
+ * about 44 significant bits, no FP64 instructions; GB300 has 2 FP64 lanes per
+ * SM against 128 FP32).  The FP64 form always uses FP64.  Errors: LBM_ERR_ARG. */
+lbm_status lbm_set_eos_arith(lbm_ctx *ctx, int mode);
 lbm_status lbm_get_tuning(const lbm_ctx *ctx, int *single_pass, int *tile, int *z_planes);
 
 /* Steps taken since the last init or lbm_set_populations. */

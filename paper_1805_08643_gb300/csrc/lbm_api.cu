@@ -32,6 +32,7 @@ struct lbm_ctx {
   void *scratch = nullptr;
   bool onepass = false;     // single-pass kernel (FP32 arithmetic forms)
   bool onepass_tma = false; // ... in its bulk-copy variant
+  bool eos_f2 = false;      // EOS radicand in compensated FP32 pairs (psi pass)
   int tile = 1, zc = 0;     // its tile shape and z planes per CTA (0 = automatic)
   bool owns = false, have_buffers = false, initialized = false, psi_valid = false;
   long long steps = 0;
@@ -133,7 +134,7 @@ cudaError_t timed(lbm_ctx *c, int kind, F &&launch) {
 
 lbm_status refresh_psi(lbm_ctx *c) {
   if (c->psi_valid) return LBM_OK;
-  CK(lbm::launch_psi(c->P, c->precision, c->g[c->cur], cur_psi(c), err_word(c), c->L), "psi kernel");
+  CK(lbm::launch_psi(c->P, c->precision, c->g[c->cur], cur_psi(c), err_word(c), c->L, c->eos_f2), "psi kernel");
   c->psi_valid = true;
   return LBM_OK;
 }
@@ -320,7 +321,7 @@ lbm_status lbm_step(lbm_ctx *c, int n) {
       c->psi_valid = true;
     } else {
       void *psi = cur_psi(c);
-      CK(timed(c, 0, [&] { return lbm::launch_psi(c->P, c->precision, gin, psi, err_word(c), c->L); }),
+      CK(timed(c, 0, [&] { return lbm::launch_psi(c->P, c->precision, gin, psi, err_word(c), c->L, c->eos_f2); }),
          "psi kernel");
       CK(timed(c, 1, [&] {
            return lbm::launch_fused(c->P, c->precision, c->op, c->sigma_on, gin, gout, psi, c->L);
@@ -449,6 +450,14 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
   if (c->onepass_tma) tile = lbm::kTile32x8;
   c->tile = tile;
   c->zc = z_planes;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_eos_arith(lbm_ctx *c, int mode) {
+  if (!c || mode < 0 || mode > 1) return fail(c, LBM_ERR_ARG, "bad EOS arithmetic mode");
+  if (mode == 1 && c->precision == LBM_F64) return fail(c, LBM_ERR_ARG, "the FP64 form evaluates its EOS in FP64");
+  c->eos_f2 = mode == 1;
+  c->psi_valid = false;
   return LBM_OK;
 }
 

@@ -150,6 +150,57 @@ __device__ __forceinline__ PsiT eos_psi(double rho, float rho_f, const KParams &
   return (PsiT)(xf * rsqrtf(xf * (one_m * one_m * one_m)));
 }
 
+// Compensated FP32 arithmetic on unevaluated sums hi + lo of two floats
+// (error-free transformations: Knuth's TwoSum, Dekker's Fast2Sum, the exact
+// product error by FMA).  The intrinsics keep the compiler from contracting or
+// reassociating the steps.
+struct F2 {
+  float h, l;
+};
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const F2 s = two_sum(a.h, b.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  const float e = __fmaf_rn(a.h, b.h, -p);
+  return fast_two_sum(p, __fadd_rn(e, __fadd_rn(__fmul_rn(a.h, b.l), __fmul_rn(a.l, b.h))));
+}
+
+// psi in FP32 with the radicand X evaluated in compensated FP32 pairs instead
+// of FP64 (about 44 significant bits; GB300 has two FP64 lanes per SM against
+// 128 FP32).  rho = rho_ref + drho is formed exactly.  The checks and the final
+// root are those of eos_psi's FP32-psi path, so psi agrees with it wherever the
+// pair's leading float equals the FP64 radicand rounded to FP32.
+template <int EOS>
+__device__ __forceinline__ float eos_psi_f2(float drho, const KParams &P, unsigned &err) {
+  const float nan = __int_as_float(0x7fc00000);
+  if (EOS == kEosNone) return 0.f;
+  const float rho_f = P.frho_ref + drho;
+  if (!isfinite(rho_f)) { err |= kErrNonFinite; return nan; }
+  if (!(rho_f > 0.0f)) { err |= kErrEosDomain; return nan; }
+  if (EOS == kEosExp) return (float)(P.psi0 * exp(-P.rho0 / (P.rho_ref + (double)drho)));
+  if (!(rho_f < P.f_rho_max)) { err |= kErrEosDomain; return nan; }
+  F2 rho = two_sum(P.rr_h, drho);
+  rho = fast_two_sum(rho.h, __fadd_rn(rho.l, P.rr_l));
+  F2 acc = {P.qh[4], P.ql[4]};
+#pragma unroll
+  for (int k = 3; k >= 0; --k) acc = f2_add(f2_mul(acc, rho), F2{P.qh[k], P.ql[k]});
+  const float xf = f2_mul(acc, rho).h;
+  if (!(xf >= 0.0f)) { err |= kErrEosDomain; return nan; }
+  if (xf == 0.0f) return 0.f;
+  const float one_m = fmaf(-P.fb4, rho_f, 1.0f);
+  return xf * rsqrtf(xf * (one_m * one_m * one_m));
+}
+
 // ------------------------------------------------------------------ force
 // S = sum_a w_a psi(x + e_a) e_a with w = 1/6 (axes), 1/12 (diagonals);
 // F = -G psi(x) S (Eq. 15).  p[a] = psi(x + e_a).

@@ -37,6 +37,9 @@ struct KParams {
   float f_rho_max;   // 4 / b: the packing limit eta < 1
   // FP32 copies for the reduced-precision kernels (no conversions on device)
   float fG, frho_ref, fs_e, fs_nu, fs_q, fs_pi, fs_eps, fs_m, fsigma_coef, fb4;
+  // the radicand coefficients and rho_ref as unevaluated sums of two floats
+  // (hi + lo), for the compensated-FP32 evaluation of the EOS
+  float qh[5], ql[5], rr_h, rr_l;
 };
 
 // Layout of the scratch buffer.
@@ -70,6 +73,13 @@ inline void refresh_float_params(KParams &P) {
   P.fs_m = (float)P.s_m;
   P.fsigma_coef = (float)P.sigma_coef;
   P.fb4 = (float)P.b4;
+  const double q[5] = {P.q0, P.q1, P.q2, P.q3, P.q4};
+  for (int k = 0; k < 5; ++k) {
+    P.qh[k] = (float)q[k];
+    P.ql[k] = (float)(q[k] - (double)P.qh[k]);
+  }
+  P.rr_h = (float)P.rho_ref;
+  P.rr_l = (float)(P.rho_ref - (double)P.rr_h);
 }
 
 // x-y tile shapes of the single-pass kernel.
@@ -110,8 +120,9 @@ size_t storage_bytes(int precision);  // bytes per stored population
 size_t psi_elem_bytes(int precision);
 
 // One time step is launch_psi followed by launch_fused (buffers swapped by the caller).
+// df: evaluate the EOS radicand in compensated FP32 pairs (FP32 / FP16 forms)
 cudaError_t launch_psi(const KParams &P, int precision, const void *g, void *psi,
-                       unsigned *err, const Launch &L);
+                       unsigned *err, const Launch &L, bool df = false);
 cudaError_t launch_fused(const KParams &P, int precision, int op, bool sigma,
                          const void *g_in, void *g_out, const void *psi, const Launch &L);
 

@@ -36,7 +36,7 @@ __device__ __forceinline__ bool node_of_thread(const KParams &P, int &x, int &y,
 }
 
 // ------------------------------------------------------------------ psi pass
-template <int PREC, int EOS>
+template <int PREC, int EOS, bool DF>
 __global__ void __launch_bounds__(256) psi_kernel(const typename Types<PREC>::S *__restrict__ g,
                                                   typename Types<PREC>::Psi *__restrict__ psi,
                                                   const KParams P, unsigned *__restrict__ err) {
@@ -53,9 +53,13 @@ __global__ void __launch_bounds__(256) psi_kernel(const typename Types<PREC>::S 
                 ((f[15] + f[16]) + (f[17] + f[18]));
   const T drho = f[0] + sax + sdg;
   unsigned e = 0;
-  const double rho = P.rho_ref + (double)drho;
-  const float rho_f = sizeof(T) == sizeof(double) ? (float)rho : Phys<T>::rho_ref(P) + (float)drho;
-  psi[nb.self] = eos_psi<EOS, typename Types<PREC>::Psi>(rho, rho_f, P, e);
+  if (DF && sizeof(T) == sizeof(float)) {
+    psi[nb.self] = (typename Types<PREC>::Psi)eos_psi_f2<EOS>((float)drho, P, e);
+  } else {
+    const double rho = P.rho_ref + (double)drho;
+    const float rho_f = sizeof(T) == sizeof(double) ? (float)rho : Phys<T>::rho_ref(P) + (float)drho;
+    psi[nb.self] = eos_psi<EOS, typename Types<PREC>::Psi>(rho, rho_f, P, e);
+  }
   if (e) atomicOr(err, e);
 }
 
@@ -313,20 +317,20 @@ dim3 node_grid(const KParams &P, const Launch &L) {
   return dim3((P.nx + L.bx - 1) / L.bx, (P.ny + L.by - 1) / L.by, P.nz);
 }
 
-template <int PREC>
+template <int PREC, bool DF>
 cudaError_t psi_dispatch(const KParams &P, const void *g, void *psi, unsigned *err, const Launch &L) {
   using S = typename Types<PREC>::S;
   using Psi = typename Types<PREC>::Psi;
   const dim3 grid = node_grid(P, L), block(L.bx, L.by);
   switch (P.eos) {
     case kEosCS:
-      psi_kernel<PREC, kEosCS><<<grid, block, 0, L.stream>>>((const S *)g, (Psi *)psi, P, err);
+      psi_kernel<PREC, kEosCS, DF><<<grid, block, 0, L.stream>>>((const S *)g, (Psi *)psi, P, err);
       break;
     case kEosExp:
-      psi_kernel<PREC, kEosExp><<<grid, block, 0, L.stream>>>((const S *)g, (Psi *)psi, P, err);
+      psi_kernel<PREC, kEosExp, DF><<<grid, block, 0, L.stream>>>((const S *)g, (Psi *)psi, P, err);
       break;
     default:
-      psi_kernel<PREC, kEosNone><<<grid, block, 0, L.stream>>>((const S *)g, (Psi *)psi, P, err);
+      psi_kernel<PREC, kEosNone, DF><<<grid, block, 0, L.stream>>>((const S *)g, (Psi *)psi, P, err);
       break;
   }
   return cudaGetLastError();
@@ -348,11 +352,11 @@ cudaError_t fused_dispatch(const KParams &P, bool sigma, const void *g_in, void 
 }  // namespace
 
 cudaError_t launch_psi(const KParams &P, int precision, const void *g, void *psi, unsigned *err,
-                       const Launch &L) {
+                       const Launch &L, bool df) {
   switch (precision) {
-    case kF64: return psi_dispatch<kF64>(P, g, psi, err, L);
-    case kF32: return psi_dispatch<kF32>(P, g, psi, err, L);
-    default: return psi_dispatch<kF16>(P, g, psi, err, L);
+    case kF64: return psi_dispatch<kF64, false>(P, g, psi, err, L);
+    case kF32: return df ? psi_dispatch<kF32, true>(P, g, psi, err, L) : psi_dispatch<kF32, false>(P, g, psi, err, L);
+    default: return df ? psi_dispatch<kF16, true>(P, g, psi, err, L) : psi_dispatch<kF16, false>(P, g, psi, err, L);
   }
 }
 

@@ -143,3 +143,38 @@ def test_bulk_copy_mode_rejects_unsupported_boxes():
     with pytest.raises(LBMError, match="ERR_ARG"):
         lat.set_tuning("tma")  # FP32 storage only
     lat.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("op", OPS)
+def test_compensated_fp32_eos_matches_fp64_eos(prec, op):
+    """The radicand in FP32 pairs rounds to the same FP32 psi as the FP64 radicand (almost everywhere)."""
+    grid = (32, 32, 32)
+    out = {}
+    for mode in ("f64", "f32x2"):
+        phys = physics(T_over_Tc=0.8)
+        rl, rv = coexistence(0.8)
+        lat = lattice(grid, op, prec, phys)
+        lat.set_eos_arith(mode)
+        lat.init_droplet((16.0, 16.0, 16.0), 8.0, 2.0, rl, rv)
+        lat.step(100)
+        assert lat.check() == 0
+        out[mode] = lat.moments()
+        lat.close()
+    d_rho, d_u = max_abs(out["f64"][0], out["f32x2"][0]), max_abs(out["f64"][1], out["f32x2"][1])
+    print(f"{prec} {op}: FP64 vs compensated-FP32 EOS after 100 steps: |drho| {d_rho:.1e} |du| {d_u:.1e}")
+    assert d_rho <= 1e-6 and d_u <= 1e-6
+
+
+def test_compensated_fp32_eos_against_oracle(oracle_runs):
+    grid = (24, 20, 28)
+    rho_o, u_o = oracle_runs(grid, "nonorth")
+    phys = physics(T_over_Tc=0.8)
+    rl, rv = coexistence(0.8)
+    lat = lattice(grid, "nonorth", "f32", phys)
+    lat.set_eos_arith("f32x2")
+    lat.init_droplet(tuple(n / 2 for n in grid), 8.0, 2.0, rl, rv)
+    lat.step(200)
+    rho, u = lat.moments()
+    lat.close()
+    assert max_abs(rho, rho_o) <= TOL["f32"] and max_abs(u, u_o) <= TOL["f32"]
