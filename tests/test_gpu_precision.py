@@ -59,7 +59,7 @@ def _run(grid, op, prec, steps, single_pass=True, tile=1, zc=0):
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
 @pytest.mark.parametrize("op", OPS)
-@pytest.mark.parametrize("grid", [(32, 32, 32), (24, 20, 28)])
+@pytest.mark.parametrize("grid", [(32, 32, 32), (24, 20, 28), (25, 20, 28)])
 @pytest.mark.parametrize("single_pass", [True, False])
 def test_reduced_precision_against_fp64_oracle(oracle_runs, prec, op, grid, single_pass):
     rho_o, u_o = oracle_runs(grid, op)
