@@ -168,6 +168,13 @@ lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
  * tile or z_planes.  Errors: LBM_ERR_ARG. */
 lbm_status lbm_set_tuning(lbm_ctx *ctx, int single_pass, int tile, int z_planes);
 
+/* Density-dependent shear viscosity (Sec. IV D: raising nu_V / nu_L lowers the
+ * spurious currents; the paper gives no rule).  nu(rho) is linear in rho from
+ * nu_v at rho_v to nu_l at rho_l and clamped between the two; each node relaxes
+ * its shear moments with s_nu(rho) = 1 / (3 nu(rho) + 1/2) in place of s_nu.
+ * nu_l <= 0 and nu_v <= 0 switch it off (the default).  Errors: LBM_ERR_ARG. */
+lbm_status lbm_set_variable_viscosity(lbm_ctx *ctx, double rho_l, double rho_v, double nu_l, double nu_v);
+
 /* Arithmetic of the EOS radicand in the psi pass of the FP32-arithmetic forms:
  * 0 (the default) FP64; 1 compensated FP32 pairs (error-free transformations,
  * about 44 significant bits, no FP64 instructions; GB300 has 2 FP64 lanes per

@@ -144,6 +144,13 @@ class Params:
     s_eps: float = 1.1
     s_m: float = 1.1
     sigma: float = 0.0
+    # density-dependent shear viscosity (Sec. IV D, last paragraph): nu varies
+    # linearly in rho from nu_v at rho_v to nu_l at rho_l, clamped between the
+    # two; s_nu(rho) = 1 / (3 nu + 1/2).  Off when nu_l is None.
+    nu_l: float | None = None
+    nu_v: float | None = None
+    rho_l_nu: float = 1.0
+    rho_v_nu: float = 0.0
 
     def with_(self, **kw) -> "Params":
         return replace(self, **kw)
@@ -165,6 +172,19 @@ def relaxation(p: Params) -> np.ndarray:
     else:
         raise ValueError(f"unknown operator {p.operator!r}")
     return np.array(d, dtype=np.float64)
+
+
+def shear_rate_field(p: Params, rho: np.ndarray) -> np.ndarray:
+    """s_nu at every node: constant, or from the density-dependent viscosity."""
+    if p.nu_l is None:
+        return np.full(np.shape(rho), p.s_nu)
+    t = (np.asarray(rho) - p.rho_v_nu) / (p.rho_l_nu - p.rho_v_nu)
+    nu = p.nu_v + t * (p.nu_l - p.nu_v)
+    nu = np.clip(nu, min(p.nu_l, p.nu_v), max(p.nu_l, p.nu_v))
+    return 1.0 / (3.0 * nu + 0.5)
+
+
+SHEAR_ROWS = {"nonorth": [5, 6, 7, 8, 9], "orth": [9, 11, 13, 14, 15]}
 
 
 def matrix(p: Params) -> np.ndarray:
@@ -354,7 +374,11 @@ def collide(p: Params, f: np.ndarray, rho: np.ndarray, u: np.ndarray,
             # the post-collision populations, M_o (M^-1 delta_4) in moments.
             G = G + np.multiply.outer(inverse(nonorth_matrix())[:, 4], sigma_term(p, F, psi))
         S = _apply(orth_matrix(), G)
-    L = lam.reshape((Q,) + (1,) * rho.ndim)
+    L = np.broadcast_to(lam.reshape((Q,) + (1,) * rho.ndim), (Q,) + rho.shape).copy()
+    if p.nu_l is not None:
+        snu = shear_rate_field(p, rho)
+        for k in SHEAR_ROWS[p.operator]:
+            L[k] = snu
     mstar = m - L * (m - meq) + (1 - L / 2) * S
     return _apply(Minv, mstar)
 

@@ -453,6 +453,24 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_variable_viscosity(lbm_ctx *c, double rho_l, double rho_v, double nu_l, double nu_v) {
+  if (!c) return LBM_ERR_ARG;
+  if (nu_l <= 0.0 && nu_v <= 0.0) {
+    c->P.varnu = 0;
+    return LBM_OK;
+  }
+  if (!(std::isfinite(rho_l) && std::isfinite(rho_v) && rho_l != rho_v && nu_l > 0.0 && nu_v > 0.0))
+    return fail(c, LBM_ERR_ARG, "need rho_l != rho_v and positive nu_l, nu_v");
+  c->P.varnu = 1;
+  c->P.nu_v = nu_v;
+  c->P.rho_v_nu = rho_v;
+  c->P.nu_slope = (nu_l - nu_v) / (rho_l - rho_v);
+  c->P.nu_lo = std::min(nu_l, nu_v);
+  c->P.nu_hi = std::max(nu_l, nu_v);
+  lbm::refresh_float_params(c->P);
+  return LBM_OK;
+}
+
 lbm_status lbm_set_eos_arith(lbm_ctx *c, int mode) {
   if (!c || mode < 0 || mode > 1) return fail(c, LBM_ERR_ARG, "bad EOS arithmetic mode");
   if (mode == 1 && c->precision == LBM_F64) return fail(c, LBM_ERR_ARG, "the FP64 form evaluates its EOS in FP64");

@@ -218,14 +218,30 @@ __device__ __forceinline__ void psi_gradient(const T p[19], T &Sx, T &Sy, T &Sz)
 template <typename T> struct Rates;
 template <> struct Rates<double> {
   double se, snu, sq, spi, seps, sm;
+  bool varnu;
+  double nu_v, rho_v, nu_slope, nu_lo, nu_hi;
   __device__ __forceinline__ explicit Rates(const KParams &P)
-      : se(P.s_e), snu(P.s_nu), sq(P.s_q), spi(P.s_pi), seps(P.s_eps), sm(P.s_m) {}
+      : se(P.s_e), snu(P.s_nu), sq(P.s_q), spi(P.s_pi), seps(P.s_eps), sm(P.s_m), varnu(P.varnu != 0),
+        nu_v(P.nu_v), rho_v(P.rho_v_nu), nu_slope(P.nu_slope), nu_lo(P.nu_lo), nu_hi(P.nu_hi) {}
 };
 template <> struct Rates<float> {
   float se, snu, sq, spi, seps, sm;
+  bool varnu;
+  float nu_v, rho_v, nu_slope, nu_lo, nu_hi;
   __device__ __forceinline__ explicit Rates(const KParams &P)
-      : se(P.fs_e), snu(P.fs_nu), sq(P.fs_q), spi(P.fs_pi), seps(P.fs_eps), sm(P.fs_m) {}
+      : se(P.fs_e), snu(P.fs_nu), sq(P.fs_q), spi(P.fs_pi), seps(P.fs_eps), sm(P.fs_m), varnu(P.varnu != 0),
+        nu_v(P.fnu_v), rho_v(P.frho_v_nu), nu_slope(P.fnu_slope), nu_lo(P.fnu_lo), nu_hi(P.fnu_hi) {}
 };
+
+// Shear rate at density rho: constant, or 1 / (3 nu(rho) + 1/2) with nu linear
+// in rho between the phases and clamped to the two phase values.
+template <typename T>
+__device__ __forceinline__ T shear_rate(const Rates<T> &r, T rho) {
+  if (!r.varnu) return r.snu;
+  T nu = r.nu_v + (rho - r.rho_v) * r.nu_slope;
+  nu = nu < r.nu_lo ? r.nu_lo : (nu > r.nu_hi ? r.nu_hi : nu);
+  return T(1) / (T(3) * nu + T(0.5));
+}
 
 // Parameters in the arithmetic type of a kernel (FP32 kernels read the float copies).
 template <typename T> struct Phys;
@@ -282,6 +298,7 @@ __device__ __forceinline__ void collide_nonorth(T f[19], T rho_ref, T Fx, T Fy, 
   // macroscopic quantities, Eq. 6
   const T rho = rho_ref + drho;
   const T inv_rho = T(1) / rho;
+  const T snu = shear_rate(r, rho);
   const T rux = jx + T(0.5) * Fx, ruy = jy + T(0.5) * Fy, ruz = jz + T(0.5) * Fz;
   const T ux = rux * inv_rho, uy = ruy * inv_rho, uz = ruz * inv_rho;
   const T qxx = rux * ux, qyy = ruy * uy, qzz = ruz * uz;  // rho u_i^2
@@ -292,11 +309,11 @@ __device__ __forceinline__ void collide_nonorth(T f[19], T rho_ref, T Fx, T Fy, 
   // relaxed moments (Eq. 4 with Eqs. 11, 13, 14)
   const T mm1 = jx + Fx, mm2 = jy + Fy, mm3 = jz + Fz;
   const T mm4 = relax(m4, drho + usq, T(2) * (Fux + Fuy + Fuz) + dS4, r.se);
-  const T mm5 = relax(m5, T(2) * qxx - qyy - qzz, T(2) * (T(2) * Fux - Fuy - Fuz), r.snu);
-  const T mm6 = relax(m6, qyy - qzz, T(2) * (Fuy - Fuz), r.snu);
-  const T mm7 = relax(m7, rux * uy, Fx * uy + Fy * ux, r.snu);
-  const T mm8 = relax(m8, rux * uz, Fx * uz + Fz * ux, r.snu);
-  const T mm9 = relax(m9, ruy * uz, Fy * uz + Fz * uy, r.snu);
+  const T mm5 = relax(m5, T(2) * qxx - qyy - qzz, T(2) * (T(2) * Fux - Fuy - Fuz), snu);
+  const T mm6 = relax(m6, qyy - qzz, T(2) * (Fuy - Fuz), snu);
+  const T mm7 = relax(m7, rux * uy, Fx * uy + Fy * ux, snu);
+  const T mm8 = relax(m8, rux * uz, Fx * uz + Fz * ux, snu);
+  const T mm9 = relax(m9, ruy * uz, Fy * uz + Fz * uy, snu);
   const T mm10 = relax(m10, third * ruy, third * Fy, r.sq);
   const T mm11 = relax(m11, third * rux, third * Fx, r.sq);
   const T mm12 = relax(m12, third * ruz, third * Fz, r.sq);
@@ -379,6 +396,7 @@ __device__ __forceinline__ void collide_orth(T f[19], T rho_ref, T Fx, T Fy, T F
   // macroscopic quantities, Eq. 6
   const T rho = rho_ref + drho;
   const T inv_rho = T(1) / rho;
+  const T snu = shear_rate(r, rho);
   const T rux = jx + T(0.5) * Fx, ruy = jy + T(0.5) * Fy, ruz = jz + T(0.5) * Fz;
   const T ux = rux * inv_rho, uy = ruy * inv_rho, uz = ruz * inv_rho;
   const T qxx = rux * ux, qyy = ruy * uy, qzz = ruz * uz;
@@ -395,13 +413,13 @@ __device__ __forceinline__ void collide_orth(T f[19], T rho_ref, T Fx, T Fy, T F
   const T mm4 = relax(m4, -two3 * rux, -two3 * Fx, r.sq);
   const T mm6 = relax(m6, -two3 * ruy, -two3 * Fy, r.sq);
   const T mm8 = relax(m8, -two3 * ruz, -two3 * Fz, r.sq);
-  const T mm9 = relax(m9, pxx, T(2) * Sxx, r.snu);
+  const T mm9 = relax(m9, pxx, T(2) * Sxx, snu);
   const T mm10 = relax(m10, T(-0.5) * pxx, -Sxx, r.spi);
-  const T mm11 = relax(m11, pww, T(2) * Sww, r.snu);
+  const T mm11 = relax(m11, pww, T(2) * Sww, snu);
   const T mm12 = relax(m12, T(-0.5) * pww, -Sww, r.spi);
-  const T mm13 = relax(m13, rux * uy, Fx * uy + Fy * ux, r.snu);
-  const T mm14 = relax(m14, ruy * uz, Fy * uz + Fz * uy, r.snu);
-  const T mm15 = relax(m15, rux * uz, Fx * uz + Fz * ux, r.snu);
+  const T mm13 = relax(m13, rux * uy, Fx * uy + Fy * ux, snu);
+  const T mm14 = relax(m14, ruy * uz, Fy * uz + Fz * uy, snu);
+  const T mm15 = relax(m15, rux * uz, Fx * uz + Fz * ux, snu);
   const T sm1 = T(1) - r.sm;
   const T mm16 = sm1 * m16, mm17 = sm1 * m17, mm18 = sm1 * m18;
   // inverse: f*_a = sum_k M_o[k][a] m*_k / |row k|^2

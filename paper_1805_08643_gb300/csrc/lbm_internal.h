@@ -37,6 +37,11 @@ struct KParams {
   float f_rho_max;   // 4 / b: the packing limit eta < 1
   // FP32 copies for the reduced-precision kernels (no conversions on device)
   float fG, frho_ref, fs_e, fs_nu, fs_q, fs_pi, fs_eps, fs_m, fsigma_coef, fb4;
+  // density-dependent shear viscosity: nu(rho) = nu_v + (rho - rho_v) nu_slope,
+  // clamped to [nu_lo, nu_hi]; s_nu(rho) = 1 / (3 nu + 1/2).  Off unless varnu.
+  int varnu;
+  double nu_v, rho_v_nu, nu_slope, nu_lo, nu_hi;
+  float fnu_v, frho_v_nu, fnu_slope, fnu_lo, fnu_hi;
   // the radicand coefficients and rho_ref as unevaluated sums of two floats
   // (hi + lo), for the compensated-FP32 evaluation of the EOS
   float qh[5], ql[5], rr_h, rr_l;
@@ -78,6 +83,11 @@ inline void refresh_float_params(KParams &P) {
     P.qh[k] = (float)q[k];
     P.ql[k] = (float)(q[k] - (double)P.qh[k]);
   }
+  P.fnu_v = (float)P.nu_v;
+  P.frho_v_nu = (float)P.rho_v_nu;
+  P.fnu_slope = (float)P.nu_slope;
+  P.fnu_lo = (float)P.nu_lo;
+  P.fnu_hi = (float)P.nu_hi;
   P.rr_h = (float)P.rho_ref;
   P.rr_l = (float)(P.rho_ref - (double)P.rr_h);
 }

@@ -59,6 +59,7 @@ SIGNATURES = {
     "lbm_kernel_times": (_c_int, [_vp, _dp, _llp, _dp, _llp]),
     "lbm_set_tuning": (_c_int, [_vp, _c_int, _c_int, _c_int]),
     "lbm_set_eos_arith": (_c_int, [_vp, _c_int]),
+    "lbm_set_variable_viscosity": (_c_int, [_vp, _c_double, _c_double, _c_double, _c_double]),
     "lbm_get_tuning": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "lbm_step_count": (ctypes.c_longlong, [_vp]),
     "lbm_step_static": (_c_int, [_vp, _vp, _vp]),
@@ -260,6 +261,10 @@ class Lattice:
         """single_pass: False / True (register-prefetch kernel) / "tma" (bulk-copy kernel)."""
         mode = 2 if single_pass == "tma" else int(bool(single_pass))
         self._check(lib.lbm_set_tuning(self._h, mode, int(tile), int(z_planes)), "lbm_set_tuning")
+
+    def set_variable_viscosity(self, rho_l, rho_v, nu_l, nu_v):
+        """nu linear in rho between (rho_v, nu_v) and (rho_l, nu_l), clamped; nu_l = nu_v = 0 switches it off."""
+        self._check(lib.lbm_set_variable_viscosity(self._h, rho_l, rho_v, nu_l, nu_v), "lbm_set_variable_viscosity")
 
     def set_eos_arith(self, mode="f64"):
         """EOS radicand arithmetic of the psi pass: "f64" or "f32x2" (compensated FP32 pairs)."""

@@ -158,3 +158,16 @@ def test_check_interval_stops_the_step_loop():
         lat.step(5)
     assert lat.steps == 1
     lat.close()
+
+
+@pytest.mark.parametrize("op", OPS)
+def test_variable_viscosity_parity(op):
+    rl, rv = coexistence(0.8)
+    lat, p, f0 = _droplet_case((24, 20, 28), op)
+    lat.set_variable_viscosity(rl, rv, 0.05, 0.25)
+    p = p.with_(nu_l=0.05, nu_v=0.25, rho_l_nu=rl, rho_v_nu=rv)
+    lat.step(100)
+    rho, u = lat.moments()
+    rho_o, u_o, _, _ = L.macroscopic(p, L.run(p, f0, 100))
+    assert max_abs(rho, rho_o) <= TOL_F64 and max_abs(u, u_o) <= TOL_F64
+    lat.close()

@@ -199,3 +199,37 @@ def test_vectorised_step_matches_brute_force_loops(op):
     u = RNG.uniform(-0.02, 0.02, (3, 5, 4, 3))
     f = L.equilibrium_state(p, rho, u) + RNG.normal(0, 1e-4, (19, 5, 4, 3))
     assert np.max(np.abs(L.step(p, f) - _brute_force_step(p, f))) < 1e-15
+
+
+# ---------------------------------------------------------------- variable viscosity
+@pytest.mark.parametrize("op", OPS)
+def test_variable_viscosity_reduces_to_constant_when_equal(op):
+    p = _droplet_params(op=op)
+    f0 = _droplet_state(p)
+    nu = (1 / p.s_nu - 0.5) / 3
+    q = p.with_(nu_l=nu, nu_v=nu, rho_l_nu=0.3, rho_v_nu=0.02)
+    assert np.max(np.abs(L.run(p, f0, 10) - L.run(q, f0, 10))) < 1e-15
+
+
+@pytest.mark.parametrize("op", OPS)
+@pytest.mark.parametrize("phase", ["liquid", "vapour"])
+def test_variable_viscosity_shear_wave_takes_the_phase_viscosity(op, phase):
+    """A uniform fluid at rho_L (rho_V) decays with nu_L (nu_V): Eq. 54 with s_nu(rho)."""
+    nz, steps = 64, 200
+    rho_l, rho_v, nu_l, nu_v = 1.2, 0.8, 0.05, 0.2
+    rho0 = rho_l if phase == "liquid" else rho_v
+    p = L.Params(grid=(3, 3, nz), operator=op, eos="none", G=0.0, s_nu=1.0, s_e=0.9, s_q=1.2, s_pi=1.3,
+                 s_eps=1.1, s_m=1.4, nu_l=nu_l, nu_v=nu_v, rho_l_nu=rho_l, rho_v_nu=rho_v)
+    k = 2 * np.pi / nz
+    z = np.broadcast_to(np.arange(nz)[:, None, None], (nz, 3, 3))
+    u = np.zeros((3, nz, 3, 3))
+    u[0] = 1e-4 * np.sin(k * z)
+    f = L.equilibrium_state(p, np.full((nz, 3, 3), rho0), u)
+
+    def amp(f):
+        return 2 * np.mean(L.macroscopic(p, f)[1][0] * np.sin(k * z))
+
+    ratio = amp(L.run(p, f, steps)) / amp(f)
+    nu = nu_l if phase == "liquid" else nu_v
+    assert abs(ratio / np.exp(-nu * k * k * steps) - 1) < 0.003
+    assert np.allclose(L.shear_rate_field(p, np.array([2.0, 0.1])), [1 / (3 * nu_l + 0.5), 1 / (3 * nu_v + 0.5)])
