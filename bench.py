@@ -448,6 +448,8 @@ def main():
     ap.add_argument("--forms", default="all", help="'all' or 'headline'")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--eos-arith", default="f64", choices=["f64", "f32x2"],
+                    help="EOS radicand arithmetic of the psi pass (FP32 / FP16 forms)")
     ap.add_argument("--study", default=None, choices=["precision"],
                     help="run a study instead of the benchmark line (minutes)")
     ap.add_argument("--study-steps", type=int, default=5000)
@@ -474,7 +476,7 @@ def main():
 
     op, prec = args.op, args.prec
     ms, kt, clocks, status = time_form(op, prec, args.edge, args.steps, args.warmup, world, clocks_index=local,
-                                       single_pass=bool(args.single_pass))
+                                       single_pass=bool(args.single_pass), eos_arith=args.eos_arith)
     ms = max_over_ranks(ms, world)
     ms_step = ms / args.steps
     value = sum_over_ranks(n * args.steps / (ms / 1e3) / 1e6, world)  # all ranks' nodes / max time
