@@ -214,6 +214,78 @@ __device__ __forceinline__ void psi_gradient(const T p[19], T &Sx, T &Sy, T &Sz)
   Sz = sixth * (p[5] - p[6]) + twelfth * ((d1112 - d1314) + (d1516 - d1718));
 }
 
+// ------------------------------------------------------------------ packed pairs
+// V2 holds one FP32 quantity of two x-adjacent nodes; its arithmetic issues one
+// packed FP32 instruction (add, multiply, fused multiply-add on float2, sm_100
+// family) for both nodes.  A product stays unevaluated (V2Mul) until it is
+// added to something, so "c + a * b" becomes one packed FMA: the contraction
+// the compiler applies to the scalar FP32 code.  The instructions carry an
+// explicit round-to-nearest modifier, which rules out any further contraction
+// by the compiler: every kernel built on V2 rounds exactly where the source
+// says.  Division and the shear-rate evaluation act lane by lane.  The
+// collision templates run on V2 unchanged.
+__device__ __forceinline__ float2 pk_add(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 pk_mul(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\t"
+      "mov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+      "mov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+struct V2 {
+  float2 v;
+  V2() = default;
+  __device__ __forceinline__ V2(float2 a) : v(a) {}
+  __device__ __forceinline__ V2(float a, float b) : v(make_float2(a, b)) {}
+  __device__ __forceinline__ explicit V2(double c) : v(make_float2((float)c, (float)c)) {}
+};
+__device__ __forceinline__ V2 v2neg(V2 a) { return V2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ V2 v2fma(V2 a, V2 b, V2 c) { return pk_fma(a.v, b.v, c.v); }
+struct V2Mul {
+  V2 a, b;
+  __device__ __forceinline__ operator V2() const { return pk_mul(a.v, b.v); }
+};
+__device__ __forceinline__ V2 operator+(V2 a, V2 b) { return pk_add(a.v, b.v); }
+__device__ __forceinline__ V2 operator-(V2 a, V2 b) { return pk_add(a.v, v2neg(b).v); }
+__device__ __forceinline__ V2 operator-(V2 a) { return v2neg(a); }
+__device__ __forceinline__ V2Mul operator*(V2 a, V2 b) { return {a, b}; }
+__device__ __forceinline__ V2 operator/(V2 a, V2 b) { return V2(a.v.x / b.v.x, a.v.y / b.v.y); }
+__device__ __forceinline__ V2 operator+(V2Mul p, V2 c) { return v2fma(p.a, p.b, c); }
+__device__ __forceinline__ V2 operator+(V2 c, V2Mul p) { return v2fma(p.a, p.b, c); }
+__device__ __forceinline__ V2 operator-(V2 c, V2Mul p) { return v2fma(v2neg(p.a), p.b, c); }
+__device__ __forceinline__ V2 operator-(V2Mul p, V2 c) { return v2fma(p.a, p.b, v2neg(c)); }
+__device__ __forceinline__ V2 operator+(V2Mul p, V2Mul q) { return v2fma(p.a, p.b, V2(q)); }
+__device__ __forceinline__ V2 operator-(V2Mul p, V2Mul q) { return v2fma(v2neg(q.a), q.b, V2(p)); }
+__device__ __forceinline__ V2Mul operator-(V2Mul p) { return {v2neg(p.a), p.b}; }
+__device__ __forceinline__ V2Mul operator*(V2Mul p, V2 c) { return {V2(p), c}; }
+__device__ __forceinline__ V2Mul operator*(V2 c, V2Mul p) { return {c, V2(p)}; }
+
 // ------------------------------------------------------------------ collision
 template <typename T> struct Rates;
 template <> struct Rates<double> {
@@ -233,6 +305,13 @@ template <> struct Rates<float> {
         nu_v(P.fnu_v), rho_v(P.frho_v_nu), nu_slope(P.fnu_slope), nu_lo(P.fnu_lo), nu_hi(P.fnu_hi) {}
 };
 
+template <> struct Rates<V2> {
+  Rates<float> s;  // scalar copy, for the density-dependent shear rate
+  V2 se, snu, sq, spi, seps, sm;
+  __device__ __forceinline__ explicit Rates(const KParams &P)
+      : s(P), se(s.se), snu(s.snu), sq(s.sq), spi(s.spi), seps(s.seps), sm(s.sm) {}
+};
+
 // Shear rate at density rho: constant, or 1 / (3 nu(rho) + 1/2) with nu linear
 // in rho between the phases and clamped to the two phase values.
 template <typename T>
@@ -241,6 +320,10 @@ __device__ __forceinline__ T shear_rate(const Rates<T> &r, T rho) {
   T nu = r.nu_v + (rho - r.rho_v) * r.nu_slope;
   nu = nu < r.nu_lo ? r.nu_lo : (nu > r.nu_hi ? r.nu_hi : nu);
   return T(1) / (T(3) * nu + T(0.5));
+}
+__device__ __forceinline__ V2 shear_rate(const Rates<V2> &r, V2 rho) {
+  if (!r.s.varnu) return r.snu;
+  return V2(shear_rate(r.s, rho.v.x), shear_rate(r.s, rho.v.y));
 }
 
 // Parameters in the arithmetic type of a kernel (FP32 kernels read the float copies).
@@ -260,6 +343,9 @@ template <> struct Phys<float> {
 template <typename T>
 __device__ __forceinline__ T relax(T m, T meq, T S, T s) {
   return m + s * (meq - m) + (T(1) - T(0.5) * s) * S;
+}
+__device__ __forceinline__ V2 relax(V2 m, V2 meq, V2 S, V2 s) {
+  return m + s * (meq - m) + (V2(1.0) - V2(0.5) * s) * S;
 }
 
 // Non-orthogonal operator: forward chains of Eq. 12, equilibria Eq. 13,

@@ -126,11 +126,13 @@ bool onepass_tma_supported(const KParams &P, int precision);
 cudaError_t launch_onepass_tma(const KParams &P, int precision, int op, bool sigma, int zc, const void *g_in,
                                void *g_out, const void *psi_in, void *psi_out, unsigned *err, cudaStream_t s);
 
-// FP16-storage two-pass kernels with two x-adjacent nodes per thread (Nx even).
-bool h2_supported(const KParams &P);
-cudaError_t launch_psi_h2(const KParams &P, const void *g, void *psi, unsigned *err, const Launch &L, bool df);
-cudaError_t launch_fused_h2(const KParams &P, int op, bool sigma, const void *g_in, void *g_out, const void *psi,
-                            const Launch &L);
+// Two-pass kernels of the FP32-arithmetic forms with two x-adjacent nodes per
+// thread and packed FP32 arithmetic (Nx even).
+bool pair_supported(const KParams &P, int precision);
+cudaError_t launch_psi_pair(const KParams &P, int precision, const void *g, void *psi, unsigned *err,
+                            const Launch &L, bool df);
+cudaError_t launch_fused_pair(const KParams &P, int precision, int op, bool sigma, const void *g_in, void *g_out,
+                              const void *psi, const Launch &L);
 
 size_t storage_bytes(int precision);  // bytes per stored population
 size_t psi_elem_bytes(int precision);

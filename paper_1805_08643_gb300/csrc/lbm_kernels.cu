@@ -355,16 +355,18 @@ cudaError_t launch_psi(const KParams &P, int precision, const void *g, void *psi
                        const Launch &L, bool df) {
   switch (precision) {
     case kF64: return psi_dispatch<kF64, false>(P, g, psi, err, L);
-    case kF32: return df ? psi_dispatch<kF32, true>(P, g, psi, err, L) : psi_dispatch<kF32, false>(P, g, psi, err, L);
+    case kF32:
+      if (pair_supported(P, precision)) return launch_psi_pair(P, precision, g, psi, err, L, df);
+      return df ? psi_dispatch<kF32, true>(P, g, psi, err, L) : psi_dispatch<kF32, false>(P, g, psi, err, L);
     default:
-      if (h2_supported(P)) return launch_psi_h2(P, g, psi, err, L, df);
+      if (pair_supported(P, precision)) return launch_psi_pair(P, precision, g, psi, err, L, df);
       return df ? psi_dispatch<kF16, true>(P, g, psi, err, L) : psi_dispatch<kF16, false>(P, g, psi, err, L);
   }
 }
 
 cudaError_t launch_fused(const KParams &P, int precision, int op, bool sigma, const void *g_in, void *g_out,
                          const void *psi, const Launch &L) {
-  if (precision == kF16 && h2_supported(P)) return launch_fused_h2(P, op, sigma, g_in, g_out, psi, L);
+  if (pair_supported(P, precision)) return launch_fused_pair(P, precision, op, sigma, g_in, g_out, psi, L);
   if (op == kNonOrth) {
     switch (precision) {
       case kF64: return fused_dispatch<kF64, kNonOrth>(P, sigma, g_in, g_out, psi, L);

@@ -1,0 +1,137 @@
+// Two-pass kernels for the FP32-arithmetic forms with two x-adjacent nodes per
+// thread (Nx even).
+//
+// A thread owns the pair (x, x+1), x even.  Populations that arrive along
+// e_x = 0 come from an aligned pair (x, x+1) of the source row: one 64-bit
+// load (FP32 storage) or 32-bit load (FP16 storage).  Those with e_x = +1 come
+// from (x-1, x) and those with e_x = -1 from (x+1, x+2), read as two scalars.
+// The psi neighbourhood is read the same way: the nine rows of the stencil as
+// aligned pairs plus x-1 and x+2 where a direction moves in x.  All arithmetic
+// of the two nodes runs on packed FP32 pairs (V2): per node it is the
+// arithmetic of the one-node kernels in lbm_kernels.cu, and a packed
+// instruction issues the work of two nodes.
+#include <cuda_fp16.h>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+#include "lbm_pair.cuh"
+
+namespace lbm {
+namespace {
+
+// psi(x + e_a) of both nodes, p[a] (Eq. 15 stencil).
+__device__ __forceinline__ void gather_psi_pair(const float *__restrict__ psi, const Nbhd &nb, const PairX &px,
+                                                V2 p[19]) {
+  // a row with x-moving directions: centre pair, x - 1 and x + 2
+  auto row3 = [&](int row, V2 &c, V2 &plus, V2 &minus) {
+    const float2 m = __ldg((const float2 *)(psi + row + px.x));
+    const float l = __ldg(psi + row + px.xm1), r = __ldg(psi + row + px.xp2);
+    c = V2(m);
+    plus = V2(m.y, r);   // psi(x + 1), psi(x + 2)
+    minus = V2(l, m.x);  // psi(x - 1), psi(x)
+  };
+  auto row1 = [&](int row) { return V2(__ldg((const float2 *)(psi + row + px.x))); };
+  row3(nb.r00, p[0], p[1], p[2]);
+  row3(nb.rp0, p[3], p[7], p[10]);
+  row3(nb.rm0, p[4], p[9], p[8]);
+  row3(nb.r0p, p[5], p[11], p[14]);
+  row3(nb.r0m, p[6], p[13], p[12]);
+  p[15] = row1(nb.rpp);
+  p[16] = row1(nb.rmm);
+  p[17] = row1(nb.rpm);
+  p[18] = row1(nb.rmp);
+}
+
+__device__ __forceinline__ bool pair_of_thread(const KParams &P, PairX &px, int &y, int &z) {
+  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  y = blockIdx.y * blockDim.y + threadIdx.y;
+  z = blockIdx.z;
+  if (x >= P.nx || y >= P.ny) return false;
+  px.x = x;
+  px.xm1 = x == 0 ? P.nx - 1 : x - 1;
+  px.xp2 = x + 2 >= P.nx ? x + 2 - P.nx : x + 2;
+  return true;
+}
+
+template <typename S, int EOS, bool DF>
+__global__ void __launch_bounds__(128) psi_pair_kernel(const S *__restrict__ g, float *__restrict__ psi,
+                                                       const KParams P, unsigned *__restrict__ err) {
+  PairX px;
+  int y, z;
+  if (!pair_of_thread(P, px, y, z)) return;
+  const Nbhd nb(px.x, y, z, P);
+  V2 f[19];
+  pull_pair<S>(g, (unsigned)P.n, nb, px, f);
+  unsigned e = 0;
+  *(float2 *)(psi + nb.self) = psi_pair<EOS, DF>(drho_pair(f), P, e);
+  if (e) atomicOr(err, e);
+}
+
+template <typename S, int OP, bool SIGMA>
+__global__ void __launch_bounds__(128) fused_pair_kernel(const S *__restrict__ g_in, S *__restrict__ g_out,
+                                                         const float *__restrict__ psi, const KParams P) {
+  PairX px;
+  int y, z;
+  if (!pair_of_thread(P, px, y, z)) return;
+  const Nbhd nb(px.x, y, z, P);
+  V2 f[19];
+  pull_pair<S>(g_in, (unsigned)P.n, nb, px, f);
+  V2 p[19];
+  gather_psi_pair(psi, nb, px, p);
+  force_collide_pair<OP, SIGMA>(f, p, P, Rates<V2>(P), OP);
+#pragma unroll
+  for (int a = 0; a < 19; ++a) PairIO<S>::st2(g_out + (size_t)a * P.n + nb.self, a, f[a]);
+}
+
+dim3 pair_grid(const KParams &P, const Launch &L) {
+  return dim3((P.nx / 2 + 31) / 32, (P.ny + L.by - 1) / L.by, P.nz);
+}
+
+template <typename S, bool DF>
+cudaError_t psi_pair_dispatch(const KParams &P, const void *g, void *psi, unsigned *err, const Launch &L) {
+  const dim3 grid = pair_grid(P, L), block(32, L.by);
+  const S *gg = (const S *)g;
+  float *pp = (float *)psi;
+  switch (P.eos) {
+    case kEosCS: psi_pair_kernel<S, kEosCS, DF><<<grid, block, 0, L.stream>>>(gg, pp, P, err); break;
+    case kEosExp: psi_pair_kernel<S, kEosExp, DF><<<grid, block, 0, L.stream>>>(gg, pp, P, err); break;
+    default: psi_pair_kernel<S, kEosNone, false><<<grid, block, 0, L.stream>>>(gg, pp, P, err); break;
+  }
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t fused_pair_dispatch(const KParams &P, int op, bool sigma, const void *g_in, void *g_out,
+                                const void *psi, const Launch &L) {
+  const dim3 grid = pair_grid(P, L), block(32, L.by);
+  const S *gi = (const S *)g_in;
+  S *go = (S *)g_out;
+  const float *pp = (const float *)psi;
+  if (op == kNonOrth) {
+    if (sigma) fused_pair_kernel<S, kNonOrth, true><<<grid, block, 0, L.stream>>>(gi, go, pp, P);
+    else fused_pair_kernel<S, kNonOrth, false><<<grid, block, 0, L.stream>>>(gi, go, pp, P);
+  } else {
+    if (sigma) fused_pair_kernel<S, kOrth, true><<<grid, block, 0, L.stream>>>(gi, go, pp, P);
+    else fused_pair_kernel<S, kOrth, false><<<grid, block, 0, L.stream>>>(gi, go, pp, P);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool pair_supported(const KParams &P, int precision) { return precision != kF64 && P.nx % 2 == 0; }
+
+cudaError_t launch_psi_pair(const KParams &P, int precision, const void *g, void *psi, unsigned *err,
+                            const Launch &L, bool df) {
+  if (precision == kF32)
+    return df ? psi_pair_dispatch<float, true>(P, g, psi, err, L) : psi_pair_dispatch<float, false>(P, g, psi, err, L);
+  return df ? psi_pair_dispatch<__half, true>(P, g, psi, err, L) : psi_pair_dispatch<__half, false>(P, g, psi, err, L);
+}
+
+cudaError_t launch_fused_pair(const KParams &P, int precision, int op, bool sigma, const void *g_in, void *g_out,
+                              const void *psi, const Launch &L) {
+  if (precision == kF32) return fused_pair_dispatch<float>(P, op, sigma, g_in, g_out, psi, L);
+  return fused_pair_dispatch<__half>(P, op, sigma, g_in, g_out, psi, L);
+}
+
+}  // namespace lbm

@@ -1,0 +1,113 @@
+// Pair access for the kernels that give each thread two x-adjacent nodes
+// (x even, Nx even): loads and stores of stored populations as pairs, the pull
+// of both nodes' 19 populations (Eq. 5), their density, psi, force and
+// collision on packed FP32 pairs (V2).
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+// Loads and stores of a pair of stored populations, decoded to FP32 deviations.
+template <typename S> struct PairIO;
+template <> struct PairIO<float> {
+  static __device__ __forceinline__ float2 ld2(const float *p) { return __ldg((const float2 *)p); }
+  static __device__ __forceinline__ float ld1(const float *p) { return __ldg(p); }
+  static __device__ __forceinline__ V2 decode(float2 v, int a) { (void)a; return V2(v); }
+  static __device__ __forceinline__ void st2(float *p, int a, V2 v) { (void)a; *(float2 *)p = v.v; }
+};
+template <> struct PairIO<__half> {
+  static __device__ __forceinline__ float2 ld2(const __half *p) { return __half22float2(__ldg((const __half2 *)p)); }
+  static __device__ __forceinline__ float ld1(const __half *p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ V2 decode(float2 v, int a) { return V2(v) * V2(lattice_w(a)); }
+  static __device__ __forceinline__ void st2(__half *p, int a, V2 v) {
+    *(__half2 *)p = __float22half2_rn(V2(v * V2((double)lattice_inv_w(a))).v);
+  }
+};
+
+// Row offset (y', z' part of the node index) of the pull source of direction a.
+__device__ __forceinline__ int src_row(const Nbhd &nb, int a) {
+  switch (a) {
+    case 0: case 1: case 2: return nb.r00;
+    case 3: case 7: case 10: return nb.rm0;
+    case 4: case 8: case 9: return nb.rp0;
+    case 5: case 11: case 14: return nb.r0m;
+    case 6: case 12: case 13: return nb.r0p;
+    case 15: return nb.rmm;
+    case 16: return nb.rpp;
+    case 17: return nb.rmp;
+    default: return nb.rpm;
+  }
+}
+
+__device__ __forceinline__ constexpr int ex_of(int a) {
+  return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1 : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
+}
+
+// x positions of a pair: x (even), x - 1 and x + 2 wrapped periodically.
+struct PairX {
+  int x, xm1, xp2;
+};
+
+// Pull the 19 deviations of nodes x and x + 1 (Eq. 5).  Populations with
+// e_x = 0 come from an aligned pair of the source row, those with e_x = +1
+// from (x-1, x) and those with e_x = -1 from (x+1, x+2), read as two scalars.
+template <typename S>
+__device__ __forceinline__ void pull_pair(const S *__restrict__ g, unsigned n, const Nbhd &nb, const PairX &px,
+                                          V2 f[19]) {
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    const S *rowp = g + (size_t)a * n + src_row(nb, a);
+    float2 v;
+    if (ex_of(a) == 0)
+      v = PairIO<S>::ld2(rowp + px.x);
+    else if (ex_of(a) > 0)
+      v = make_float2(PairIO<S>::ld1(rowp + px.xm1), PairIO<S>::ld1(rowp + px.x));
+    else
+      v = make_float2(PairIO<S>::ld1(rowp + px.x + 1), PairIO<S>::ld1(rowp + px.xp2));
+    f[a] = PairIO<S>::decode(v, a);
+  }
+}
+
+// rho - rho_ref of both nodes: the sum of the pulled deviations (Eq. 6).
+__device__ __forceinline__ V2 drho_pair(const V2 f[19]) {
+  const V2 sax = (f[1] + f[2]) + (f[3] + f[4]) + (f[5] + f[6]);
+  const V2 sdg = ((f[7] + f[8]) + (f[9] + f[10])) + ((f[11] + f[12]) + (f[13] + f[14])) +
+                 ((f[15] + f[16]) + (f[17] + f[18]));
+  return f[0] + sax + sdg;
+}
+
+// psi of both nodes from rho - rho_ref; DF selects the compensated-FP32 radicand.
+template <int EOS, bool DF>
+__device__ __forceinline__ float2 psi_pair(V2 drho, const KParams &P, unsigned &e) {
+  float out[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float d = k == 0 ? drho.v.x : drho.v.y;
+    if (DF)
+      out[k] = eos_psi_f2<EOS>(d, P, e);
+    else
+      out[k] = eos_psi<EOS, float>(P.rho_ref + (double)d, P.frho_ref + d, P, e);
+  }
+  return make_float2(out[0], out[1]);
+}
+
+// Force (Eq. 15, with the Eq. 16 term when SIGMA) and collision of both nodes,
+// from p[a] = psi(x + e_a).  OP is kOrth, kNonOrth or 2 (then op_rt picks).
+template <int OP, bool SIGMA>
+__device__ __forceinline__ void force_collide_pair(V2 f[19], const V2 p[19], const KParams &P, const Rates<V2> &r,
+                                                   int op_rt) {
+  V2 Sx, Sy, Sz;
+  psi_gradient<V2>(p, Sx, Sy, Sz);
+  const V2 kk = V2((double)-P.fG) * p[0];
+  const V2 dS4 = SIGMA ? V2(V2((double)P.fsigma_coef) * V2(Sx * Sx + Sy * Sy + Sz * Sz)) : V2(0.0);
+  const V2 Fx = kk * Sx, Fy = kk * Sy, Fz = kk * Sz;
+  if (OP == kNonOrth || (OP == 2 && op_rt == kNonOrth))
+    collide_nonorth<V2>(f, V2((double)P.frho_ref), Fx, Fy, Fz, dS4, r);
+  else
+    collide_orth<V2>(f, V2((double)P.frho_ref), Fx, Fy, Fz, dS4, r);
+}
+
+}  // namespace lbm
