@@ -56,10 +56,10 @@ FUSED_BYTES = {"f64": 19 * 8 * 2 + 8, "f32": 19 * 4 * 2 + 4, "f16": 19 * 2 * 2 +
 # ... and of the psi pass: 19 populations read + psi written
 PSI_BYTES = {"f64": 19 * 8 + 8, "f32": 19 * 4 + 4, "f16": 19 * 2 + 4}
 HEADLINE = ("nonorth", "f32")
-# DRAM bytes per node of the fused pass from one ncu capture at 256^3 (profiles/fused_psi_nonorth_f32.md);
-# null for forms without a capture of the current kernel.
-FUSED_DRAM_BYTES = {("nonorth", "f32"): 153.3}
-# FP64 instructions per node of the fused pass (ncu, profiles/fused_psi_nonorth_orth_f64.md) and the FP64
+# DRAM bytes per node of the fused pass, from one ncu capture of the current kernel at 256^3 (dram__bytes_read
+# + dram__bytes_write over the nodes); null for forms without such a capture.
+FUSED_DRAM_BYTES = {("nonorth", "f32"): 152.6, ("nonorth", "f16"): 77.4}
+# FP64 instructions per node of the fused pass (ncu instruction counts at 128^3 over the nodes) and the FP64
 # issue peak of one GB300: 2 per SM per clock x 152 SMs x 2070 MHz.
 FUSED_FP64_INSTR = {"nonorth": 255.0, "orth": 309.0}
 FP64_PEAK_GINSTR = 2 * 152 * 2070e6 / 1e9
