@@ -150,6 +150,28 @@ __device__ __forceinline__ PsiT eos_psi(double rho, float rho_f, const KParams &
   return (PsiT)(xf * rsqrtf(xf * (one_m * one_m * one_m)));
 }
 
+// psi in FP32 from d = rho - rho_ref (the FP32-arithmetic forms): the radicand
+// X as a quintic in d, Horner in FP64 from host-made coefficients (KParams::c),
+// five FMA and no separate rho_ref + d, one FP64 operation fewer than the
+// quintic in rho; checks and the final root as in eos_psi's FP32-psi path.
+template <int EOS>
+__device__ __forceinline__ float eos_psi_d(float d, const KParams &P, unsigned &err) {
+  const float nan = __int_as_float(0x7fc00000);
+  if (EOS == kEosNone) return 0.f;
+  const float rho_f = P.frho_ref + d;
+  if (!isfinite(rho_f)) { err |= kErrNonFinite; return nan; }
+  if (!(rho_f > 0.0f)) { err |= kErrEosDomain; return nan; }
+  if (EOS == kEosExp) return (float)(P.psi0 * exp(-P.rho0 / (P.rho_ref + (double)d)));
+  if (!(rho_f < P.f_rho_max)) { err |= kErrEosDomain; return nan; }
+  const double x = (double)d;
+  const double X = fma(fma(fma(fma(fma(P.c[5], x, P.c[4]), x, P.c[3]), x, P.c[2]), x, P.c[1]), x, P.c[0]);
+  const float xf = (float)X;
+  if (!(xf >= 0.0f)) { err |= kErrEosDomain; return nan; }
+  if (xf == 0.0f) return 0.f;
+  const float one_m = fmaf(-P.fb4, rho_f, 1.0f);
+  return xf * rsqrtf(xf * (one_m * one_m * one_m));
+}
+
 // Compensated FP32 arithmetic on unevaluated sums hi + lo of two floats
 // (error-free transformations: Knuth's TwoSum, Dekker's Fast2Sum, the exact
 // product error by FMA).  The intrinsics keep the compiler from contracting or

@@ -45,6 +45,8 @@ struct KParams {
   // the radicand coefficients and rho_ref as unevaluated sums of two floats
   // (hi + lo), for the compensated-FP32 evaluation of the EOS
   float qh[5], ql[5], rr_h, rr_l;
+  // the same radicand as a quintic in d = rho - rho_ref: sum_k c[k] d^k
+  double c[6];
 };
 
 // Layout of the scratch buffer.
@@ -90,6 +92,19 @@ inline void refresh_float_params(KParams &P) {
   P.fnu_hi = (float)P.nu_hi;
   P.rr_h = (float)P.rho_ref;
   P.rr_l = (float)(P.rho_ref - (double)P.rr_h);
+  // X(rho) = sum_{m=1..5} q[m-1] rho^m with rho = rho_ref + d:
+  // c[k] = sum_{m >= max(k, 1)} q[m-1] binom(m, k) rho_ref^(m-k)
+  static const double binom[6][6] = {{1, 0, 0, 0, 0, 0},  {1, 1, 0, 0, 0, 0},   {1, 2, 1, 0, 0, 0},
+                                     {1, 3, 3, 1, 0, 0},  {1, 4, 6, 4, 1, 0},   {1, 5, 10, 10, 5, 1}};
+  for (int k = 0; k <= 5; ++k) {
+    double acc = 0.0;
+    for (int m = k > 1 ? k : 1; m <= 5; ++m) {
+      double rp = 1.0;
+      for (int j = 0; j < m - k; ++j) rp *= P.rho_ref;
+      acc += q[m - 1] * binom[m][k] * rp;
+    }
+    P.c[k] = acc;
+  }
 }
 
 // x-y tile shapes of the single-pass kernel.

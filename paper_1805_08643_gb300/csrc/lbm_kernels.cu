@@ -55,6 +55,8 @@ __global__ void __launch_bounds__(256) psi_kernel(const typename Types<PREC>::S 
   unsigned e = 0;
   if (DF && sizeof(T) == sizeof(float)) {
     psi[nb.self] = (typename Types<PREC>::Psi)eos_psi_f2<EOS>((float)drho, P, e);
+  } else if (sizeof(T) == sizeof(float)) {
+    psi[nb.self] = (typename Types<PREC>::Psi)eos_psi_d<EOS>((float)drho, P, e);
   } else {
     const double rho = P.rho_ref + (double)drho;
     const float rho_f = sizeof(T) == sizeof(double) ? (float)rho : Phys<T>::rho_ref(P) + (float)drho;

@@ -89,7 +89,7 @@ __device__ __forceinline__ float2 psi_pair(V2 drho, const KParams &P, unsigned &
     if (DF)
       out[k] = eos_psi_f2<EOS>(d, P, e);
     else
-      out[k] = eos_psi<EOS, float>(P.rho_ref + (double)d, P.frho_ref + d, P, e);
+      out[k] = eos_psi_d<EOS>(d, P, e);
   }
   return make_float2(out[0], out[1]);
 }
