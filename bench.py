@@ -450,7 +450,7 @@ def main():
     ap.add_argument("--op", default=HEADLINE[0], choices=["nonorth", "orth"])
     ap.add_argument("--prec", default=HEADLINE[1], choices=["f64", "f32", "f16"])
     ap.add_argument("--single-pass", type=int, default=0, help="1: single-pass kernel (FP32 arithmetic forms)")
-    ap.add_argument("--forms", default="all", help="'all' or 'headline'")
+    ap.add_argument("--forms", default="all", help="'all', 'headline' or 'batched' (headline + batched + served)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--eos-arith", default="f64", choices=["f64", "f32x2"],
@@ -542,7 +542,7 @@ def main():
                                              "hbm_frac_fused": FUSED_BYTES[fprec] * n / (f_fused / 1e3) / 1e9 / hbm_peak,
                                              "status": fst}
 
-    if args.forms == "all":
+    if args.forms in ("all", "batched"):
         forms["batched_512"] = batched_run(args.steps, args.warmup)
         forms["served"] = served_run()
 

@@ -209,10 +209,12 @@ long long lbm_step_count(const lbm_ctx *ctx);
 lbm_status lbm_step_static(const lbm_ctx *ctx, const double *f_in, double *f_out);
 
 /* ------------------------------------------------------------------ batches
- * Many independent periodic boxes advanced together: every step is one
- * persistent launch of the single-pass kernel over a table of work items
- * (one x-y tile of one box and a range of z planes each, largest boxes first),
- * and lbm_batch_step replays the launches of two steps as a CUDA graph.  Boxes
+ * Many independent periodic boxes advanced together: every step runs
+ * persistent launches over a table of work items (one x-y tile of one box and
+ * a range of z planes each, largest boxes first): when every box has an even
+ * Nx, the fused pass and then the psi pass of the new state on the two-node
+ * kernels of lbm_step; otherwise one launch of the single-pass kernel.
+ * lbm_batch_step replays the launches of two steps as a CUDA graph.  Boxes
  * may differ in size, operator, temperature, G, rates and sigma; they share the
  * precision (LBM_F32 or LBM_F32_STORE_F16) and the kind of EOS.  Boxes join
  * (lbm_batch_add) and leave (lbm_batch_remove) between calls: continuous

@@ -1,6 +1,8 @@
-// Batched boxes: many independent periodic boxes advanced together, one
-// persistent single-pass launch per step over a table of work items, the
-// launches of two steps captured in a CUDA graph.  Boxes can join and leave
+// Batched boxes: many independent periodic boxes advanced together by
+// persistent launches over a table of work items, the launches of two steps
+// captured in a CUDA graph.  When every box has an even Nx a step is the
+// two-pass pair kernels (fused pass, then psi of the new level); otherwise it
+// is one single-pass launch.  Boxes can join and leave
 // between calls (continuous batching); each box's buffers come from the
 // stream-ordered allocator and count against the batch's HBM budget.
 #include <cuda_runtime.h>
@@ -56,6 +58,7 @@ struct lbm_batch {
   bool own_stream = false;
   int cap_red = 0;
   bool dirty = true;         // descriptors / items need uploading, graphs re-capturing
+  bool pair = false;         // the captured step is the two-pass pair kernels
   cudaGraphExec_t g2 = nullptr, g1 = nullptr;
   long long steps = 0;
   std::string err;
@@ -128,17 +131,24 @@ lbm_status rebuild(lbm_batch *b) {
     BCK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, b->stream), "H2D items");
   BCK(cudaStreamSynchronize(b->stream), "sync");  // host vectors go out of scope
   destroy_graphs(b);
+  bool pair = true;
+  for (auto &o : order) pair = pair && b->boxes[o.second].d.P.nx % 2 == 0;
+  b->pair = pair;
   if (b->nitems) {
-    const int per_sm = b->tile == lbm::kTile32x4 ? 4 : 2;  // resident blocks the kernel is sized for
+    // resident blocks the kernels are sized for
+    const int per_sm = pair ? (b->tile == lbm::kTile32x4 ? 8 : 4) : (b->tile == lbm::kTile32x4 ? 4 : 2);
     const int grid = std::min(b->grid_blocks * per_sm, b->nitems);
+    auto step = [&](int parity) {
+      return pair ? lbm::launch_batch_pair(b->precision, b->eos, b->tile, b->d_boxes, b->d_items, b->nitems, parity,
+                                           grid, b->d_err, b->stream)
+                  : lbm::launch_batch_onepass(b->precision, b->eos, b->tile, b->d_boxes, b->d_items, b->nitems,
+                                              parity, grid, b->d_err, b->stream);
+    };
     for (int k = 0; k < 2; ++k) {
       cudaGraph_t g;
       BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-      cudaError_t e = lbm::launch_batch_onepass(b->precision, b->eos, b->tile, b->d_boxes, b->d_items, b->nitems, 0,
-                                                grid, b->d_err, b->stream);
-      if (e == cudaSuccess && k == 0)
-        e = lbm::launch_batch_onepass(b->precision, b->eos, b->tile, b->d_boxes, b->d_items, b->nitems, 1, grid,
-                                      b->d_err, b->stream);
+      cudaError_t e = step(0);
+      if (e == cudaSuccess && k == 0) e = step(1);
       cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
       if (e != cudaSuccess || e2 != cudaSuccess) {
         if (e2 == cudaSuccess) cudaGraphDestroy(g);

@@ -130,6 +130,10 @@ struct BatchBox {
 
 // Persistent single-pass launch over the work items (box, tx | ty << 16, z0, z1)
 // of many boxes; grid = number of thread blocks.  FP32 arithmetic forms only.
+// The batch's two-pass step on the pair kernels (every box with an even Nx):
+// the fused pass, then the psi pass of the new level, for one parity.
+cudaError_t launch_batch_pair(int precision, int eos, int tile, const BatchBox *boxes, const int4 *items, int nitems,
+                              int parity, int grid, unsigned *err, cudaStream_t s);
 cudaError_t launch_batch_onepass(int precision, int eos, int tile, const BatchBox *boxes, const int4 *items,
                                  int nitems, int parity, int grid, unsigned *err, cudaStream_t s);
 // Block shape of a tile choice: returns threads per block, sets bx, by.

@@ -117,9 +117,94 @@ cudaError_t fused_pair_dispatch(const KParams &P, int op, bool sigma, const void
   return cudaGetLastError();
 }
 
+// Batched boxes, two-pass step: work item w = (box, tile_x | tile_y << 16, z0, z1)
+// is a TXP x TY tile of pairs (2 TXP x TY nodes) of one box through planes
+// [z0, z1).  The fused pass reads level in = cur ^ parity (populations and psi)
+// and writes the populations of level in ^ 1; the psi pass then evaluates psi
+// of level in ^ 1, so after a step psi of the current level is always valid.
+template <typename S, bool PSI, int EOS, int TXP, int TY>
+__global__ void __launch_bounds__(TXP *TY) batch_pair_kernel(const BatchBox *__restrict__ boxes,
+                                                             const int4 *__restrict__ items, int nitems, int parity,
+                                                             unsigned *__restrict__ err) {
+  __shared__ BatchBox bb;
+  const int tid = threadIdx.y * TXP + threadIdx.x;
+  unsigned e = 0;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int4 w = items[it];
+    __syncthreads();  // every thread is done with the previous item's descriptor
+    {
+      const int *src = (const int *)(boxes + w.x);
+      int *dst = (int *)&bb;
+      for (int k = tid; k < (int)(sizeof(BatchBox) / sizeof(int)); k += TXP * TY) dst[k] = src[k];
+    }
+    __syncthreads();
+    const KParams &P = bb.P;
+    const int in = bb.cur ^ parity;
+    const int x = (w.y & 0xffff) * (2 * TXP) + 2 * threadIdx.x, y = (w.y >> 16) * TY + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) continue;
+    const PairX px{x, x == 0 ? P.nx - 1 : x - 1, x + 2 >= P.nx ? x + 2 - P.nx : x + 2};
+    if (PSI) {
+      const S *g = (const S *)bb.g[in ^ 1];
+      float *psi = bb.psi[in ^ 1];
+      for (int z = w.z; z < w.w; ++z) {
+        const Nbhd nb(x, y, z, P);
+        V2 f[19];
+        pull_pair<S>(g, (unsigned)P.n, nb, px, f);
+        *(float2 *)(psi + nb.self) = psi_pair<EOS, false>(drho_pair(f), P, e);
+      }
+    } else {
+      const S *g_in = (const S *)bb.g[in];
+      S *g_out = (S *)bb.g[in ^ 1];
+      const float *psi = bb.psi[in];
+      const Rates<V2> r(P);
+      for (int z = w.z; z < w.w; ++z) {
+        const Nbhd nb(x, y, z, P);
+        V2 f[19];
+        pull_pair<S>(g_in, (unsigned)P.n, nb, px, f);
+        V2 p[19];
+        gather_psi_pair(psi, nb, px, p);
+        force_collide_pair<2, true>(f, p, P, r, bb.op);
+#pragma unroll
+        for (int a = 0; a < 19; ++a) PairIO<S>::st2(g_out + (size_t)a * P.n + nb.self, a, f[a]);
+      }
+    }
+  }
+  if (e) atomicOr(err, e);
+}
+
+template <typename S, int TXP, int TY>
+cudaError_t batch_pair_shape(int eos, const BatchBox *boxes, const int4 *items, int nitems, int parity, int grid,
+                             unsigned *err, cudaStream_t s) {
+  const dim3 block(TXP, TY);
+  batch_pair_kernel<S, false, kEosNone, TXP, TY><<<grid, block, 0, s>>>(boxes, items, nitems, parity, err);
+  switch (eos) {
+    case kEosCS: batch_pair_kernel<S, true, kEosCS, TXP, TY><<<grid, block, 0, s>>>(boxes, items, nitems, parity, err); break;
+    case kEosExp: batch_pair_kernel<S, true, kEosExp, TXP, TY><<<grid, block, 0, s>>>(boxes, items, nitems, parity, err); break;
+    default: batch_pair_kernel<S, true, kEosNone, TXP, TY><<<grid, block, 0, s>>>(boxes, items, nitems, parity, err); break;
+  }
+  return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t batch_pair_tile(int tile, int eos, const BatchBox *boxes, const int4 *items, int nitems, int parity,
+                            int grid, unsigned *err, cudaStream_t s) {
+  switch (tile) {
+    case kTile32x4: return batch_pair_shape<S, 16, 4>(eos, boxes, items, nitems, parity, grid, err, s);
+    case kTile64x4: return batch_pair_shape<S, 32, 4>(eos, boxes, items, nitems, parity, grid, err, s);
+    default: return batch_pair_shape<S, 16, 8>(eos, boxes, items, nitems, parity, grid, err, s);
+  }
+}
+
 }  // namespace
 
 bool pair_supported(const KParams &P, int precision) { return precision != kF64 && P.nx % 2 == 0; }
+
+cudaError_t launch_batch_pair(int precision, int eos, int tile, const BatchBox *boxes, const int4 *items, int nitems,
+                              int parity, int grid, unsigned *err, cudaStream_t s) {
+  if (precision == kF32) return batch_pair_tile<float>(tile, eos, boxes, items, nitems, parity, grid, err, s);
+  if (precision == kF16) return batch_pair_tile<__half>(tile, eos, boxes, items, nitems, parity, grid, err, s);
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_psi_pair(const KParams &P, int precision, const void *g, void *psi, unsigned *err,
                             const Launch &L, bool df) {
