@@ -1,4 +1,9 @@
-"""Batched boxes (one persistent launch per step) and continuous batching."""
+"""Batched boxes (persistent launches over a work-item table, CUDA graphs) and continuous batching.
+
+A batch whose boxes all have an even Nx steps on the two-pass pair kernels; one
+box with an odd Nx puts the whole batch on the single-pass kernel.  Both are
+compared with single-box runs.
+"""
 
 import numpy as np
 import pytest
@@ -65,6 +70,21 @@ def test_batch_matches_single_box_runs(steps, prec):
         tol = 1e-6 if prec == "f32" else 2e-3
         assert max_abs(rho, rho1) <= tol and max_abs(u, u1) <= tol, spec
         assert b.box_steps(box) == steps
+    b.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_batch_with_an_odd_nx_box_uses_the_single_pass_kernel(prec):
+    boxes = [((25, 20, 28), "orth", 0.8, 0.105, 2.0), BOXES[0]]
+    b = _batch(prec)
+    ids = [_add(b, s, prec) for s in boxes]
+    b.step(21)
+    assert b.check() == 0
+    for box, spec in zip(ids, boxes):
+        rho, u = b.moments(box)
+        rho1, u1 = _single(spec, 21, prec)
+        tol = 1e-6 if prec == "f32" else 2e-3
+        assert max_abs(rho, rho1) <= tol and max_abs(u, u1) <= tol, spec
     b.close()
 
 
