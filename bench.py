@@ -194,7 +194,7 @@ def time_form(op, prec, edge, steps, warmup, world, clocks_index=None, field="dr
 
     lat, rl, rv = make_lattice(op, prec, edge, SIGMA_DROPLET if field == "droplet" else SIGMA_FLAT)
     if single_pass:
-        lat.set_tuning(True, 1, 0)
+        lat.set_tuning({1: True, 2: "tma", 3: "onchip"}[int(single_pass)], 1, 0)
     if eos_arith != "f64":
         lat.set_eos_arith(eos_arith)
     if field == "droplet":
@@ -449,7 +449,8 @@ def main():
     ap.add_argument("--edge", type=int, default=EDGE)
     ap.add_argument("--op", default=HEADLINE[0], choices=["nonorth", "orth"])
     ap.add_argument("--prec", default=HEADLINE[1], choices=["f64", "f32", "f16"])
-    ap.add_argument("--single-pass", type=int, default=0, help="1: single-pass kernel (FP32 arithmetic forms)")
+    ap.add_argument("--single-pass", type=int, default=0,
+                    help="1: single-pass kernel, 2: its bulk-copy variant, 3: on-chip-psi single pass (FP32 arithmetic)")
     ap.add_argument("--forms", default="all", help="'all', 'headline' or 'batched' (headline + batched + served)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -481,7 +482,7 @@ def main():
 
     op, prec = args.op, args.prec
     ms, kt, clocks, status = time_form(op, prec, args.edge, args.steps, args.warmup, world, clocks_index=local,
-                                       single_pass=bool(args.single_pass), eos_arith=args.eos_arith)
+                                       single_pass=args.single_pass, eos_arith=args.eos_arith)
     ms = max_over_ranks(ms, world)
     ms_step = ms / args.steps
     value = sum_over_ranks(n * args.steps / (ms / 1e3) / 1e6, world)  # all ranks' nodes / max time

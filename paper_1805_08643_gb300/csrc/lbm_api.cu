@@ -32,6 +32,7 @@ struct lbm_ctx {
   void *scratch = nullptr;
   bool onepass = false;     // single-pass kernel (FP32 arithmetic forms)
   bool onepass_tma = false; // ... in its bulk-copy variant
+  bool onchip = false;      // single pass with psi evaluated on chip (FP32 arithmetic, Nx even)
   bool eos_f2 = false;      // EOS radicand in compensated FP32 pairs (psi pass)
   int tile = 1, zc = 0;     // its tile shape and z planes per CTA (0 = automatic)
   bool owns = false, have_buffers = false, initialized = false, psi_valid = false;
@@ -307,7 +308,15 @@ lbm_status lbm_step(lbm_ctx *c, int n) {
   const int zc = c->zc > 0 ? c->zc : auto_zc(c);
   for (int k = 0; k < n; ++k) {
     void *gin = c->g[c->cur], *gout = c->g[c->cur ^ 1];
-    if (c->onepass) {
+    if (c->onchip) {
+      CK(timed(c, 1, [&] {
+           return lbm::launch_onchip(c->P, c->precision, c->op, c->sigma_on, c->eos_f2, gin, gout, err_word(c),
+                                     c->L.stream);
+         }),
+         "single-pass kernel");
+      c->cur ^= 1;
+      c->psi_valid = false;
+    } else if (c->onepass) {
       void *pin = cur_psi(c), *pout = psi_at(c, c->pc ^ 1);
       CK(timed(c, 1, [&] {
            return c->onepass_tma ? lbm::launch_onepass_tma(c->P, c->precision, c->op, c->sigma_on, zc, gin, gout,
@@ -439,13 +448,16 @@ lbm_status lbm_kernel_times(lbm_ctx *c, double *ms_psi, long long *n_psi, double
 }
 
 lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
-  if (!c || single_pass < 0 || single_pass > 2 || tile < 0 || tile > 2 || z_planes < 0)
+  if (!c || single_pass < 0 || single_pass > 3 || tile < 0 || tile > 2 || z_planes < 0)
     return fail(c, LBM_ERR_ARG, "bad tuning");
   if (single_pass && c->precision == LBM_F64) return fail(c, LBM_ERR_ARG, "single pass needs FP32 arithmetic");
   if (single_pass == 2 && !lbm::onepass_tma_supported(c->P, c->precision))
     return fail(c, LBM_ERR_ARG, "bulk-copy single pass needs FP32 storage, Nx % 4 == 0 and Nx >= 40");
-  if (c->onepass != (single_pass != 0)) c->psi_valid = false;
-  c->onepass = single_pass != 0;
+  if (single_pass == 3 && !lbm::onchip_supported(c->P, c->precision))
+    return fail(c, LBM_ERR_ARG, "on-chip-psi single pass needs FP32 arithmetic and an even Nx");
+  c->psi_valid = false;
+  c->onchip = single_pass == 3;
+  c->onepass = single_pass == 1 || single_pass == 2;
   c->onepass_tma = single_pass == 2;
   if (c->onepass_tma) tile = lbm::kTile32x8;
   c->tile = tile;
@@ -481,7 +493,7 @@ lbm_status lbm_set_eos_arith(lbm_ctx *c, int mode) {
 
 lbm_status lbm_get_tuning(const lbm_ctx *c, int *single_pass, int *tile, int *z_planes) {
   if (!c) return LBM_ERR_ARG;
-  if (single_pass) *single_pass = c->onepass ? (c->onepass_tma ? 2 : 1) : 0;
+  if (single_pass) *single_pass = c->onchip ? 3 : c->onepass ? (c->onepass_tma ? 2 : 1) : 0;
   if (tile) *tile = c->tile;
   if (z_planes) *z_planes = c->zc > 0 ? c->zc : auto_zc(c);
   return LBM_OK;

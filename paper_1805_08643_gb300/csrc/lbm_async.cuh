@@ -1,0 +1,43 @@
+// Shared-memory barriers (mbarrier) used by the single-pass kernels.  Every
+// wait is bounded: a wait that gives up returns false and the caller records
+// kErrTimeout and stops, so no thread can hang on a barrier.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// Arrive once (release: the caller's earlier shared-memory accesses are ordered before it).
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Wait (acquire) for the phase with the given parity to complete; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+}  // namespace lbm

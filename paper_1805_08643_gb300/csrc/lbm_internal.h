@@ -153,6 +153,12 @@ cudaError_t launch_psi_pair(const KParams &P, int precision, const void *g, void
 cudaError_t launch_fused_pair(const KParams &P, int precision, int op, bool sigma, const void *g_in, void *g_out,
                               const void *psi, const Launch &L);
 
+// Single-pass step with psi evaluated on chip by producer warps and the
+// collision run by consumer warps (FP32 arithmetic, Nx even); no psi array.
+bool onchip_supported(const KParams &P, int precision);
+cudaError_t launch_onchip(const KParams &P, int precision, int op, bool sigma, bool df, const void *g_in, void *g_out,
+                          unsigned *err, cudaStream_t s);
+
 size_t storage_bytes(int precision);  // bytes per stored population
 size_t psi_elem_bytes(int precision);
 

@@ -17,6 +17,7 @@
 // Requirements (checked by the launcher): nx % 4 == 0 and nx >= BX + 8.
 #include <cuda_runtime.h>
 
+#include "lbm_async.cuh"
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -26,34 +27,6 @@ namespace {
 __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
-}
-
-__device__ __forceinline__ unsigned smem_addr(const void *p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-
-// Wait for the phase with the given parity to complete; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
-  const unsigned a = smem_addr(bar);
-  for (int it = 0; it < (1 << 22); ++it) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
 }
 
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {

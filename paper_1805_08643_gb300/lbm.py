@@ -258,8 +258,14 @@ class Lattice:
         self._check(lib.lbm_set_check_interval(self._h, int(k)), "lbm_set_check_interval")
 
     def set_tuning(self, single_pass=True, tile=1, z_planes=0):
-        """single_pass: False / True (register-prefetch kernel) / "tma" (bulk-copy kernel)."""
-        mode = 2 if single_pass == "tma" else int(bool(single_pass))
+        """single_pass: False / True (register-prefetch kernel) / "tma" (bulk-copy kernel) /
+        "onchip" (psi evaluated on chip by producer warps; Nx even)."""
+        if isinstance(single_pass, str):
+            if single_pass not in ("tma", "onchip"):
+                raise ValueError(f"unknown single_pass mode {single_pass!r}")
+            mode = 2 if single_pass == "tma" else 3
+        else:
+            mode = int(bool(single_pass))
         self._check(lib.lbm_set_tuning(self._h, mode, int(tile), int(z_planes)), "lbm_set_tuning")
 
     def set_variable_viscosity(self, rho_l, rho_v, nu_l, nu_v):
@@ -273,7 +279,8 @@ class Lattice:
     def tuning(self):
         sp, t, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._check(lib.lbm_get_tuning(self._h, ctypes.byref(sp), ctypes.byref(t), ctypes.byref(z)), "lbm_get_tuning")
-        return {"single_pass": {0: False, 1: True, 2: "tma"}[sp.value], "tile": t.value, "z_planes": z.value}
+        return {"single_pass": {0: False, 1: True, 2: "tma", 3: "onchip"}[sp.value], "tile": t.value,
+                "z_planes": z.value}
 
     def set_profiling(self, on=True):
         self._check(lib.lbm_set_profiling(self._h, 1 if on else 0), "lbm_set_profiling")
