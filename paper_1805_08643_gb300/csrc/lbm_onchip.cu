@@ -9,8 +9,10 @@
 //  * Producer warps (4): for each plane, pull the populations of the tile's
 //    128 node pairs and of the ring's 52 pairs (as lbm_kernels_pair.cu), put
 //    the tile's into a shared staging buffer, sum rho, evaluate psi (Eq. 58
-//    radicand in FP64) into a four-plane psi ring and signal the plane.  They
-//    run up to three planes ahead of the consumers.
+//    radicand in FP64) into a four-plane psi ring and signal the plane.  The
+//    pulls of the next plane are in flight while psi of one is evaluated, L2
+//    is asked for the plane after, and producers run up to three planes ahead
+//    of the consumers.
 //  * Consumer warps (4): for plane z, once psi of plane z+1 is signalled, take
 //    the staged populations of plane z and psi of planes z-1, z, z+1 from
 //    shared memory, apply force and collision on packed FP32 pairs (as
@@ -51,6 +53,16 @@ constexpr size_t kSmemBytes = kRingOff;
 __device__ __forceinline__ int wrapi(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
+}
+
+// Ask L2 for the lines that the pull of pair (x, x+1), row y, plane z will read
+// (one line per direction; the shifted neighbours x-1, x+2 share it or the next).
+template <typename S>
+__device__ __forceinline__ void prefetch_pair_l2(const S *__restrict__ g, const KParams &P, int x, int y, int z) {
+  const Nbhd nb(x, y, z, P);
+#pragma unroll
+  for (int a = 0; a < 19; ++a)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(g + (size_t)a * P.n + src_row(nb, a) + x));
 }
 
 // Local coordinates of ring pair r: rows y = -1 and y = BY with x = -2 .. BX,
@@ -105,6 +117,15 @@ __global__ void __launch_bounds__(NTH, 2)
     const PairX pxp{gxp, gxp == 0 ? P.nx - 1 : gxp - 1, gxp + 2 >= P.nx ? gxp + 2 - P.nx : gxp + 2};
     const PairX pxr{rgx, rgx == 0 ? P.nx - 1 : rgx - 1, rgx + 2 >= P.nx ? rgx + 2 - P.nx : rgx + 2};
     const int m_last = z1 - z0 + 1;  // planes z0 - 1 .. z1
+    // software pipeline: the pulls of plane m + 1 are in flight while psi of
+    // plane m is evaluated
+    V2 f[19], fr[19];
+    auto pull = [&](int m) {
+      const int zw = wrapi(z0 - 1 + m, P.nz);
+      pull_pair<S>(g_in, (unsigned)P.n, Nbhd(gxp, gyp, zw, P), pxp, f);
+      if (has_ring) pull_pair<S>(g_in, (unsigned)P.n, Nbhd(rgx, rgy, zw, P), pxr, fr);
+    };
+    pull(0);
     for (int m = 0; m <= m_last; ++m) {
       // psi slot and staging buffer m & 3 last held plane m - 4; the collisions
       // up to plane m - 3 read it: wait for that one (the ((m - 4) / 4)-th
@@ -113,16 +134,19 @@ __global__ void __launch_bounds__(NTH, 2)
         e |= kErrTimeout;
         break;
       }
-      const int zw = wrapi(z0 - 1 + m, P.nz);
-      float *ps = psi_slot(m);
-      V2 f[19], fr[19];
-      pull_pair<S>(g_in, (unsigned)P.n, Nbhd(gxp, gyp, zw, P), pxp, f);
-      if (has_ring) pull_pair<S>(g_in, (unsigned)P.n, Nbhd(rgx, rgy, zw, P), pxr, fr);
       float2 *st = stage_buf(m) + p;
 #pragma unroll
       for (int a = 0; a < 19; ++a) st[a * NI] = f[a].v;
-      *(float2 *)(ps + cs) = psi_pair<EOS, DF>(drho_pair(f), P, e);
-      if (has_ring) *(float2 *)(ps + cr) = psi_pair<EOS, DF>(drho_pair(fr), P, e);
+      const V2 dt = drho_pair(f), dr = has_ring ? drho_pair(fr) : V2(0.0);
+      if (m + 1 <= m_last) pull(m + 1);
+      if (m + 2 <= m_last) {  // and L2 is asked for the plane after
+        const int zn = wrapi(z0 + 1 + m, P.nz);
+        prefetch_pair_l2<S>(g_in, P, gxp, gyp, zn);
+        if (has_ring) prefetch_pair_l2<S>(g_in, P, rgx, rgy, zn);
+      }
+      float *ps = psi_slot(m);
+      *(float2 *)(ps + cs) = psi_pair<EOS, DF>(dt, P, e);
+      if (has_ring) *(float2 *)(ps + cr) = psi_pair<EOS, DF>(dr, P, e);
       mbar_arrive(&full[m & 3]);
     }
   } else {
