@@ -255,7 +255,8 @@ def e2e_run(op, prec, edge, steps):
 
 
 def batched_run(steps, warmup, n_boxes=512):
-    """The batched workload: n_boxes periodic boxes (edges 32/48/64/96), one launch per step."""
+    """The batched workload: n_boxes periodic boxes (edges 32/48/64/96); every edge is even, so each step is
+    the fused pass and the psi pass of the pair kernels over the work-item table (two launches)."""
     import torch
 
     from paper_1805_08643_gb300 import synth, thermo, tune
@@ -289,7 +290,8 @@ def batched_run(steps, warmup, n_boxes=512):
     batch.close()
     return {"mlups": nodes * steps / (ms / 1e3) / 1e6, "ms_per_step": ms / steps, "boxes": n_boxes, "nodes": nodes,
             "work_items": info["work_items"], "tile": tune.TILES[tile], "z_planes": zc,
-            "step_gbs": (2 * 19 * 4 + 8) * nodes / (ms / steps / 1e3) / 1e9,
+            "step_gbs": (FUSED_BYTES["f32"] + PSI_BYTES["f32"]) * nodes / (ms / steps / 1e3) / 1e9,
+            "bytes_per_lup": FUSED_BYTES["f32"] + PSI_BYTES["f32"],
             "tuning_ms_per_step": {f"{tune.TILES[t]}/z{z}": round(v, 3) for (t, z), v in table.items()},
             "operators": "alternating non-orthogonal / orthogonal", "status": status,
             "physics": "a=0.25, W=5, sigma=0.105, T/Tc~U[0.6,0.9], R~U[6,edge/3], FP32"}
@@ -452,6 +454,7 @@ def main():
     ap.add_argument("--single-pass", type=int, default=0,
                     help="1: single-pass kernel, 2: its bulk-copy variant, 3: on-chip-psi single pass (FP32 arithmetic)")
     ap.add_argument("--forms", default="all", help="'all', 'headline' or 'batched' (headline + batched + served)")
+    ap.add_argument("--batch-boxes", type=int, default=512, help="boxes of the batched form")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--eos-arith", default="f64", choices=["f64", "f32x2"],
@@ -544,7 +547,7 @@ def main():
                                              "status": fst}
 
     if args.forms in ("all", "batched"):
-        forms["batched_512"] = batched_run(args.steps, args.warmup)
+        forms[f"batched_{args.batch_boxes}"] = batched_run(args.steps, args.warmup, args.batch_boxes)
         forms["served"] = served_run()
 
     e2e = None
