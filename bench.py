@@ -316,6 +316,29 @@ def served_run(n_jobs=24, load=1.0, max_steps=2000, tol=1e-7):
     return out
 
 
+def serve_study(n_jobs=40, loads=(0.5, 1.0, 2.0), max_steps=2000, tol=1e-8):
+    """The served configuration: Poisson streams of droplet / slab jobs, box edges U[48, 192], T/T_c U[0.6, 0.9],
+    random operator, FP32, run until max|du| < tol per 100 steps (or max_steps); offered rate swept as multiples
+    of a capacity estimate (20 GLUPS over jobs of mean edge^3 x max_steps).  p50 / p99 time from arrival to
+    convergence and aggregate MLUPS per rate."""
+    from paper_1805_08643_gb300 import synth
+    from paper_1805_08643_gb300.serve import BatchBackend, Server
+
+    lo, hi = 48, 192
+    mean_nodes = (hi ** 4 - lo ** 4) / (4 * (hi - lo))
+    capacity = 20e9 / (mean_nodes * max_steps)
+    rows = []
+    for load in loads:
+        jobs = synth.job_stream(n_jobs, rate_per_s=load * capacity, edge_lo=lo, edge_hi=hi)
+        be = BatchBackend("f32", hbm_budget_bytes=96 << 30)
+        rep = Server(be, check_every=100, tol=tol, max_steps=max_steps, min_steps=200).run(jobs)
+        be.close()
+        rows.append({"load": load, "offered_jobs_per_s": load * capacity, **rep.summary()})
+    return {"study": "serve", "jobs_per_rate": n_jobs, "edge": [lo, hi], "tol_max_du_per_100_steps": tol,
+            "max_steps": max_steps, "workload": "droplet or slab, T/Tc U[0.6,0.9], operator random, FP32, a=0.25, "
+                                                "W=5, sigma=0.105 (droplet) / 0.116 (slab)", "rates": rows}
+
+
 def precision_study(edge=512, steps=5000):
     """FP32 and FP16-storage forms against the FP64 form on the 27-droplet workload.
 
@@ -459,7 +482,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--eos-arith", default="f64", choices=["f64", "f32x2"],
                     help="EOS radicand arithmetic of the psi pass (FP32 / FP16 forms)")
-    ap.add_argument("--study", default=None, choices=["precision"],
+    ap.add_argument("--study", default=None, choices=["precision", "serve"],
                     help="run a study instead of the benchmark line (minutes)")
     ap.add_argument("--study-steps", type=int, default=5000)
     args = ap.parse_args()
@@ -479,6 +502,10 @@ def main():
     if args.study == "precision":
         if rank == 0:
             print(json.dumps(precision_study(args.edge if args.edge != EDGE else 512, args.study_steps)))
+        return
+    if args.study == "serve":
+        if rank == 0:
+            print(json.dumps(serve_study()))
         return
     n = args.edge ** 3
     hbm_peak, peak_kind = peaks()
