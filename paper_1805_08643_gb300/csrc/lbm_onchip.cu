@@ -9,10 +9,9 @@
 //  * Producer warps (4): for each plane, pull the populations of the tile's
 //    128 node pairs and of the ring's 52 pairs (as lbm_kernels_pair.cu), put
 //    the tile's into a shared staging buffer, sum rho, evaluate psi (Eq. 58
-//    radicand in FP64) into a four-plane psi ring and signal the plane.  The
-//    pulls of the next plane are in flight while psi of one is evaluated, L2
-//    is asked for the plane after, and producers run up to three planes ahead
-//    of the consumers.
+//    radicand in FP64) into a four-plane psi ring and signal the plane.  They
+//    ask L2 for the plane after next and run up to two planes ahead of the
+//    consumers (three staging buffers).
 //  * Consumer warps (4): for plane z, once psi of plane z+1 is signalled, take
 //    the staged populations of plane z and psi of planes z-1, z, z+1 from
 //    shared memory, apply force and collision on packed FP32 pairs (as
@@ -40,11 +39,11 @@ constexpr int NR = 2 * (TX + 2) + 2 * TY;  // ring pairs: two full rows (x = -2 
 constexpr int NPT = 128;                   // producer threads
 constexpr int NTH = NI + NPT;
 constexpr int PX = BX + 4, EY = BY + 2, NPSI = PX * EY;  // psi plane: local x -2 .. BX+1, y -1 .. BY
-constexpr int NSTAGE = 4;                  // staging buffers of tile pairs
+constexpr int NSTAGE = 3;                  // staging buffers of tile pairs
 static_assert(NI == NPT && NR <= NPT, "each producer thread owns one tile pair and at most one ring pair");
 
 // shared memory layout (bytes)
-constexpr size_t kBarBytes = 64;                                    // full[4], empty[4]
+constexpr size_t kBarBytes = 64;                                    // full[4], empty[3]
 constexpr size_t kPsiOff = kBarBytes;
 constexpr size_t kStageOff = kPsiOff + (sizeof(float) * 4 * NPSI + 15) / 16 * 16;
 constexpr size_t kRingOff = kStageOff + sizeof(float2) * NSTAGE * 19 * NI;  // end of the staging
@@ -80,10 +79,10 @@ __device__ __forceinline__ void ring_pair(int r, int &lx, int &ly) {
 
 // Planes of a block are counted from z0 - 1: index m = z - z0 + 1.  psi of plane
 // m lives in slot m & 3 (the (m >> 2)-th use of full[m & 3]); the staged tile
-// pairs of plane m (decoded FP32 deviations) in buffer m & 3, released through
-// empty[m & 3] once plane m is collided.
+// pairs of plane m (decoded FP32 deviations) in buffer m % 3, released through
+// empty[m % 3] once plane m is collided.
 template <typename S, int OP, bool SIGMA, int EOS, bool DF>
-__global__ void __launch_bounds__(NTH, 2)
+__global__ void __launch_bounds__(NTH, 3)
     onchip_kernel(const S *__restrict__ g_in, S *__restrict__ g_out, const KParams P, int zc,
                   unsigned *__restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -98,12 +97,12 @@ __global__ void __launch_bounds__(NTH, 2)
   const int z0 = (blockIdx.x / tiles) * zc, z1 = min(z0 + zc, P.nz);
   if (tid == 0) {
     for (int k = 0; k < 4; ++k) mbar_init(&full[k], NPT);
-    for (int k = 0; k < 4; ++k) mbar_init(&empty[k], NI);
+    for (int k = 0; k < 3; ++k) mbar_init(&empty[k], NI);
   }
   __syncthreads();
   unsigned e = 0;
   auto psi_slot = [&](int m) { return psi + (m & 3) * NPSI; };
-  auto stage_buf = [&](int m) { return stage + (m & 3) * 19 * NI; };
+  auto stage_buf = [&](int m) { return stage + (m % NSTAGE) * 19 * NI; };
 
   if (tid >= NI) {
     // ---------------------------------------------------------------- producer
@@ -117,36 +116,31 @@ __global__ void __launch_bounds__(NTH, 2)
     const PairX pxp{gxp, gxp == 0 ? P.nx - 1 : gxp - 1, gxp + 2 >= P.nx ? gxp + 2 - P.nx : gxp + 2};
     const PairX pxr{rgx, rgx == 0 ? P.nx - 1 : rgx - 1, rgx + 2 >= P.nx ? rgx + 2 - P.nx : rgx + 2};
     const int m_last = z1 - z0 + 1;  // planes z0 - 1 .. z1
-    // software pipeline: the pulls of plane m + 1 are in flight while psi of
-    // plane m is evaluated
-    V2 f[19], fr[19];
-    auto pull = [&](int m) {
-      const int zw = wrapi(z0 - 1 + m, P.nz);
-      pull_pair<S>(g_in, (unsigned)P.n, Nbhd(gxp, gyp, zw, P), pxp, f);
-      if (has_ring) pull_pair<S>(g_in, (unsigned)P.n, Nbhd(rgx, rgy, zw, P), pxr, fr);
-    };
-    pull(0);
     for (int m = 0; m <= m_last; ++m) {
-      // psi slot and staging buffer m & 3 last held plane m - 4; the collisions
-      // up to plane m - 3 read it: wait for that one (the ((m - 4) / 4)-th
-      // release of buffer (m - 3) & 3)
-      if (m >= 4 && !mbar_wait(&empty[(m - 3) & 3], ((m - 4) / 4) & 1)) {
+      // staging buffer m % 3 last held plane m - 3 and psi slot m & 3 plane m - 4:
+      // the collision of plane m - 3 is the last to read either, so wait for it
+      // (the ((m - 4) / 3)-th release of buffer (m - 3) % 3)
+      if (m >= 4 && !mbar_wait(&empty[(m - 3) % NSTAGE], ((m - 4) / NSTAGE) & 1)) {
         e |= kErrTimeout;
         break;
       }
-      float2 *st = stage_buf(m) + p;
-#pragma unroll
-      for (int a = 0; a < 19; ++a) st[a * NI] = f[a].v;
-      const V2 dt = drho_pair(f), dr = has_ring ? drho_pair(fr) : V2(0.0);
-      if (m + 1 <= m_last) pull(m + 1);
-      if (m + 2 <= m_last) {  // and L2 is asked for the plane after
+      const int zw = wrapi(z0 - 1 + m, P.nz);
+      if (m + 2 <= m_last) {  // ask L2 for the plane after next
         const int zn = wrapi(z0 + 1 + m, P.nz);
         prefetch_pair_l2<S>(g_in, P, gxp, gyp, zn);
         if (has_ring) prefetch_pair_l2<S>(g_in, P, rgx, rgy, zn);
       }
       float *ps = psi_slot(m);
-      *(float2 *)(ps + cs) = psi_pair<EOS, DF>(dt, P, e);
-      if (has_ring) *(float2 *)(ps + cr) = psi_pair<EOS, DF>(dr, P, e);
+      V2 f[19];
+      pull_pair<S>(g_in, (unsigned)P.n, Nbhd(gxp, gyp, zw, P), pxp, f);
+      float2 *st = stage_buf(m) + p;
+#pragma unroll
+      for (int a = 0; a < 19; ++a) st[a * NI] = f[a].v;
+      *(float2 *)(ps + cs) = psi_pair<EOS, DF>(drho_pair(f), P, e);
+      if (has_ring) {
+        pull_pair<S>(g_in, (unsigned)P.n, Nbhd(rgx, rgy, zw, P), pxr, f);
+        *(float2 *)(ps + cr) = psi_pair<EOS, DF>(drho_pair(f), P, e);
+      }
       mbar_arrive(&full[m & 3]);
     }
   } else {
@@ -191,7 +185,7 @@ __global__ void __launch_bounds__(NTH, 2)
 #pragma unroll
         for (int a = 0; a < 19; ++a) PairIO<S>::st2(g_out + (size_t)a * P.n + self, a, f[a]);
       }
-      mbar_arrive(&empty[m & 3]);
+      mbar_arrive(&empty[m % NSTAGE]);
     }
     if (!ok) e |= kErrTimeout;
   }
