@@ -166,8 +166,8 @@ lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
  * LBM_F32_STORE_F16, Nx even) runs each step as one kernel that evaluates psi
  * of the step on chip from the pulled populations (producer warps, for the
  * thread block's 32x8 tile and a one-node ring) while consumer warps collide:
- * no psi array is read or written, and the result is that of the default
- * two-pass step bit for bit; tile and z_planes do not apply.  tile picks the x-y tile of
+ * no psi array is read or written, and with FP32 storage the result is that
+ * of the default two-pass step bit for bit; tile and z_planes do not apply.  tile picks the x-y tile of
  * the single-pass kernel (0: 32x4, 1: 32x8, 2: 64x4); z_planes the z planes
  * each thread block marches through (0 = automatic).  Results do not depend on
  * tile or z_planes.  Errors: LBM_ERR_ARG. */
