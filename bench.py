@@ -16,7 +16,7 @@ object adds both operators in FP64 and FP32 and the FP16-storage form, all on
 the same box.  A "step" is one lattice time step (psi pass + fused pass) over
 the whole box; MLUPS = 1e-6 * nodes * steps / second.
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--quick]
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--forms headline|batched|all]
 
 Under torchrun (N > 1) each rank runs its own box on its own GPU (replicas,
 weak scaling); the timed region is bracketed by barriers and the max over
