@@ -194,7 +194,7 @@ def time_form(op, prec, edge, steps, warmup, world, clocks_index=None, field="dr
 
     lat, rl, rv = make_lattice(op, prec, edge, SIGMA_DROPLET if field == "droplet" else SIGMA_FLAT)
     if single_pass:
-        lat.set_tuning({1: True, 2: "tma", 3: "onchip"}[int(single_pass)], 1, 0)
+        lat.set_tuning({1: True, 2: "tma", 3: "onchip", 4: "lagged"}[int(single_pass)], 1, 0)
     if eos_arith != "f64":
         lat.set_eos_arith(eos_arith)
     if field == "droplet":
@@ -475,7 +475,8 @@ def main():
     ap.add_argument("--op", default=HEADLINE[0], choices=["nonorth", "orth"])
     ap.add_argument("--prec", default=HEADLINE[1], choices=["f64", "f32", "f16"])
     ap.add_argument("--single-pass", type=int, default=0,
-                    help="1: single-pass kernel, 2: its bulk-copy variant, 3: on-chip-psi single pass (FP32 arithmetic)")
+                    help="1: single-pass kernel, 2: its bulk-copy variant, 3: on-chip-psi single pass, "
+                         "4: trailing-psi single pass (FP32 arithmetic)")
     ap.add_argument("--forms", default="all", help="'all', 'headline' or 'batched' (headline + batched + served)")
     ap.add_argument("--batch-boxes", type=int, default=512, help="boxes of the batched form")
     ap.add_argument("--no-cpu", action="store_true")

@@ -167,7 +167,12 @@ lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
  * of the step on chip from the pulled populations (producer warps, for the
  * thread block's 32x8 tile and a one-node ring) while consumer warps collide:
  * no psi array is read or written, and with FP32 storage the result is that
- * of the default two-pass step bit for bit; tile and z_planes do not apply.  tile picks the x-y tile of
+ * of the default two-pass step bit for bit; tile and z_planes do not apply.
+ * 4 (same forms) runs each step as one cooperative launch in which the psi
+ * pass of the next step trails the fused pass by one plane, reading the new
+ * populations from L2; results equal the two-pass step bit for bit; the first
+ * call in this mode allocates a small device array of progress flags (one int
+ * per 64x4 tile and plane), freed by lbm_destroy.  tile picks the x-y tile of
  * the single-pass kernel (0: 32x4, 1: 32x8, 2: 64x4); z_planes the z planes
  * each thread block marches through (0 = automatic).  Results do not depend on
  * tile or z_planes.  Errors: LBM_ERR_ARG. */

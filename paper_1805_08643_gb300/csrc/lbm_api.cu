@@ -33,6 +33,10 @@ struct lbm_ctx {
   bool onepass = false;     // single-pass kernel (FP32 arithmetic forms)
   bool onepass_tma = false; // ... in its bulk-copy variant
   bool onchip = false;      // single pass with psi evaluated on chip (FP32 arithmetic, Nx even)
+  bool lagged = false;      // single pass with the next psi pass one plane behind (FP32 arithmetic, Nx even)
+  int *flags = nullptr;     // its per-(tile, plane) progress flags
+  size_t nflags = 0;
+  int stamp = 0;
   bool eos_f2 = false;      // EOS radicand in compensated FP32 pairs (psi pass)
   int tile = 1, zc = 0;     // its tile shape and z planes per CTA (0 = automatic)
   bool owns = false, have_buffers = false, initialized = false, psi_valid = false;
@@ -298,9 +302,10 @@ lbm_status lbm_step(lbm_ctx *c, int n) {
   if (!c) return LBM_ERR_ARG;
   if (n < 1) return fail(c, LBM_ERR_ARG, "n must be >= 1");
   if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_step before an init");
-  if (c->onepass && !c->psi_valid) {
+  if ((c->onepass || c->lagged) && !c->psi_valid) {
     CK(timed(c, 0, [&] {
-         return lbm::launch_psi(c->P, c->precision, c->g[c->cur], cur_psi(c), err_word(c), c->L);
+         return lbm::launch_psi(c->P, c->precision, c->g[c->cur], cur_psi(c), err_word(c), c->L,
+                                c->lagged && c->eos_f2);
        }),
        "psi kernel");
     c->psi_valid = true;
@@ -308,7 +313,18 @@ lbm_status lbm_step(lbm_ctx *c, int n) {
   const int zc = c->zc > 0 ? c->zc : auto_zc(c);
   for (int k = 0; k < n; ++k) {
     void *gin = c->g[c->cur], *gout = c->g[c->cur ^ 1];
-    if (c->onchip) {
+    if (c->lagged) {
+      void *pin = cur_psi(c), *pout = psi_at(c, c->pc ^ 1);
+      const int stamp = ++c->stamp;
+      CK(timed(c, 1, [&] {
+           return lbm::launch_lagged(c->P, c->precision, c->op, c->sigma_on, c->eos_f2, gin, gout, pin, pout,
+                                     c->flags, stamp, err_word(c), c->L.stream);
+         }),
+         "single-pass kernel");
+      c->pc ^= 1;
+      c->cur ^= 1;
+      c->psi_valid = true;
+    } else if (c->onchip) {
       CK(timed(c, 1, [&] {
            return lbm::launch_onchip(c->P, c->precision, c->op, c->sigma_on, c->eos_f2, gin, gout, err_word(c),
                                      c->L.stream);
@@ -448,14 +464,29 @@ lbm_status lbm_kernel_times(lbm_ctx *c, double *ms_psi, long long *n_psi, double
 }
 
 lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
-  if (!c || single_pass < 0 || single_pass > 3 || tile < 0 || tile > 2 || z_planes < 0)
+  if (!c || single_pass < 0 || single_pass > 4 || tile < 0 || tile > 2 || z_planes < 0)
     return fail(c, LBM_ERR_ARG, "bad tuning");
   if (single_pass && c->precision == LBM_F64) return fail(c, LBM_ERR_ARG, "single pass needs FP32 arithmetic");
   if (single_pass == 2 && !lbm::onepass_tma_supported(c->P, c->precision))
     return fail(c, LBM_ERR_ARG, "bulk-copy single pass needs FP32 storage, Nx % 4 == 0 and Nx >= 40");
   if (single_pass == 3 && !lbm::onchip_supported(c->P, c->precision))
     return fail(c, LBM_ERR_ARG, "on-chip-psi single pass needs FP32 arithmetic and an even Nx");
+  if (single_pass == 4) {
+    if (!lbm::lagged_supported(c->P, c->precision))
+      return fail(c, LBM_ERR_ARG, "trailing-psi single pass needs FP32 arithmetic and an even Nx");
+    const size_t need = lbm::lagged_flag_count(c->P);
+    if (c->nflags < need) {
+      if (c->flags) cudaFree(c->flags);
+      c->flags = nullptr;
+      c->nflags = 0;
+      CK(cudaMalloc((void **)&c->flags, need * sizeof(int)), "cudaMalloc(flags)");
+      CK(cudaMemsetAsync(c->flags, 0, need * sizeof(int), c->L.stream), "cudaMemsetAsync(flags)");
+      c->nflags = need;
+      c->stamp = 0;
+    }
+  }
   c->psi_valid = false;
+  c->lagged = single_pass == 4;
   c->onchip = single_pass == 3;
   c->onepass = single_pass == 1 || single_pass == 2;
   c->onepass_tma = single_pass == 2;
@@ -493,7 +524,7 @@ lbm_status lbm_set_eos_arith(lbm_ctx *c, int mode) {
 
 lbm_status lbm_get_tuning(const lbm_ctx *c, int *single_pass, int *tile, int *z_planes) {
   if (!c) return LBM_ERR_ARG;
-  if (single_pass) *single_pass = c->onchip ? 3 : c->onepass ? (c->onepass_tma ? 2 : 1) : 0;
+  if (single_pass) *single_pass = c->lagged ? 4 : c->onchip ? 3 : c->onepass ? (c->onepass_tma ? 2 : 1) : 0;
   if (tile) *tile = c->tile;
   if (z_planes) *z_planes = c->zc > 0 ? c->zc : auto_zc(c);
   return LBM_OK;
@@ -503,8 +534,9 @@ long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
 
 void lbm_destroy(lbm_ctx *c) {
   if (!c) return;
-  if (c->have_buffers || !c->pool.empty()) cudaStreamSynchronize(c->L.stream);
+  if (c->have_buffers || !c->pool.empty() || c->flags) cudaStreamSynchronize(c->L.stream);
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  if (c->flags) cudaFree(c->flags);
   if (c->owns) {
     cudaFree(c->g[0]);
     cudaFree(c->g[1]);

@@ -159,6 +159,15 @@ bool onchip_supported(const KParams &P, int precision);
 cudaError_t launch_onchip(const KParams &P, int precision, int op, bool sigma, bool df, const void *g_in, void *g_out,
                           unsigned *err, cudaStream_t s);
 
+// Single-pass step in which psi of the next step trails the fused pass by one
+// plane in one cooperative launch (FP32 arithmetic, Nx even).  flags: an int
+// per (tile, plane), lagged_flag_count(P) of them, zero before the first
+// launch; stamp: a number larger than in every earlier launch on these flags.
+bool lagged_supported(const KParams &P, int precision);
+size_t lagged_flag_count(const KParams &P);
+cudaError_t launch_lagged(const KParams &P, int precision, int op, bool sigma, bool df, const void *g_in, void *g_out,
+                          const void *psi_in, void *psi_out, int *flags, int stamp, unsigned *err, cudaStream_t s);
+
 size_t storage_bytes(int precision);  // bytes per stored population
 size_t psi_elem_bytes(int precision);
 

@@ -259,11 +259,13 @@ class Lattice:
 
     def set_tuning(self, single_pass=True, tile=1, z_planes=0):
         """single_pass: False / True (register-prefetch kernel) / "tma" (bulk-copy kernel) /
-        "onchip" (psi evaluated on chip by producer warps; Nx even)."""
+        "onchip" (psi evaluated on chip by producer warps; Nx even) / "lagged" (the next psi pass one plane
+        behind the fused pass in one cooperative launch; Nx even)."""
         if isinstance(single_pass, str):
-            if single_pass not in ("tma", "onchip"):
+            modes = {"tma": 2, "onchip": 3, "lagged": 4}
+            if single_pass not in modes:
                 raise ValueError(f"unknown single_pass mode {single_pass!r}")
-            mode = 2 if single_pass == "tma" else 3
+            mode = modes[single_pass]
         else:
             mode = int(bool(single_pass))
         self._check(lib.lbm_set_tuning(self._h, mode, int(tile), int(z_planes)), "lbm_set_tuning")
@@ -279,7 +281,7 @@ class Lattice:
     def tuning(self):
         sp, t, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._check(lib.lbm_get_tuning(self._h, ctypes.byref(sp), ctypes.byref(t), ctypes.byref(z)), "lbm_get_tuning")
-        return {"single_pass": {0: False, 1: True, 2: "tma", 3: "onchip"}[sp.value], "tile": t.value,
+        return {"single_pass": {0: False, 1: True, 2: "tma", 3: "onchip", 4: "lagged"}[sp.value], "tile": t.value,
                 "z_planes": z.value}
 
     def set_profiling(self, on=True):
