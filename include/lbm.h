@@ -175,7 +175,9 @@ lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
  * per 64x4 tile and plane), freed by lbm_destroy.  tile picks the x-y tile of
  * the single-pass kernel (0: 32x4, 1: 32x8, 2: 64x4); z_planes the z planes
  * each thread block marches through (0 = automatic).  Results do not depend on
- * tile or z_planes.  Errors: LBM_ERR_ARG. */
+ * tile or z_planes.  Errors: LBM_ERR_ARG (bad value, or a mode the context's
+ * precision or Nx does not support); LBM_ERR_OOM / LBM_ERR_CUDA (mode 4's flag
+ * array could not be allocated). */
 lbm_status lbm_set_tuning(lbm_ctx *ctx, int single_pass, int tile, int z_planes);
 
 /* Density-dependent shear viscosity (Sec. IV D: raising nu_V / nu_L lowers the

@@ -73,3 +73,24 @@ def test_create_validates_arguments_without_touching_the_gpu(lbm):
     assert pb.value == 19 * 512 * 2 and sb.value == 2 * 512 * 4
     lbm.lib.lbm_destroy(h)
     assert lbm.lib.lbm_status_string(4) == b"LBM_ERR_NONFINITE"
+
+
+def test_set_tuning_validates_modes_without_touching_the_gpu(lbm):
+    st, h = _create(lbm)  # FP64
+    assert st == lbm.OK
+    for mode in (1, 2, 3, 4):  # every single pass needs FP32 arithmetic
+        assert lbm.lib.lbm_set_tuning(h, mode, 1, 0) == lbm.ERR_ARG
+    assert lbm.lib.lbm_set_tuning(h, 5, 1, 0) == lbm.ERR_ARG
+    assert lbm.lib.lbm_set_tuning(h, 0, 3, 0) == lbm.ERR_ARG
+    assert lbm.lib.lbm_set_tuning(h, 0, 1, -1) == lbm.ERR_ARG
+    lbm.lib.lbm_destroy(h)
+    st, h = _create(lbm, grid=(9, 8, 8), prec=1)  # FP32, odd Nx: no two-node kernels
+    assert st == lbm.OK
+    assert lbm.lib.lbm_set_tuning(h, 3, 1, 0) == lbm.ERR_ARG
+    assert lbm.lib.lbm_set_tuning(h, 4, 1, 0) == lbm.ERR_ARG
+    assert b"even Nx" in lbm.lib.lbm_last_error(h)
+    assert lbm.lib.lbm_set_tuning(h, 1, 2, 16) == lbm.OK  # the one-node single pass takes any Nx
+    sp, t, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert lbm.lib.lbm_get_tuning(h, ctypes.byref(sp), ctypes.byref(t), ctypes.byref(z)) == lbm.OK
+    assert (sp.value, t.value, z.value) == (1, 2, 16)
+    lbm.lib.lbm_destroy(h)
