@@ -146,7 +146,7 @@ __device__ __forceinline__ void psi_plane(const S *__restrict__ g, float *__rest
 // Block b works on z chunk b / per_chunk ([z0, z1), at least three planes) and
 // on tiles b % per_chunk, + per_chunk, ... of it.
 template <typename S, int OP, bool SIGMA, int EOS, bool DF>
-__global__ void __launch_bounds__(NTH, 6) lagged_kernel(const S *__restrict__ g_in, S *__restrict__ g_out,
+__global__ void __launch_bounds__(NTH, 7) lagged_kernel(const S *__restrict__ g_in, S *__restrict__ g_out,
                                                      const float *__restrict__ psi_in, float *__restrict__ psi_out,
                                                      const KParams P, int zc, int per_chunk,
                                                      int *__restrict__ flags, int stamp, unsigned *__restrict__ err) {
