@@ -82,8 +82,11 @@ __device__ __forceinline__ void fused_plane(const S *__restrict__ g_in, S *__res
   if (x >= P.nx || y >= P.ny) return;
   const PairX px{x, x == 0 ? P.nx - 1 : x - 1, x + 2 >= P.nx ? x + 2 - P.nx : x + 2};
   const Nbhd nb(x, y, z, P);
-  V2 f[19];
-  pull_pair<S>(g_in, (unsigned)P.n, nb, px, f);
+  // the force first, from psi, then the populations: the two sets of 19 pairs
+  // are never live together, which keeps the registers (and so more blocks
+  // resident) down
+  V2 Fx, Fy, Fz, dS4;
+  {
   V2 p[19];
   auto row3 = [&](int row, V2 &c, V2 &plus, V2 &minus) {
     const float2 m = __ldg((const float2 *)(psi + row + px.x));
@@ -102,7 +105,11 @@ __device__ __forceinline__ void fused_plane(const S *__restrict__ g_in, S *__res
   p[16] = row1(nb.rmm);
   p[17] = row1(nb.rpm);
   p[18] = row1(nb.rmp);
-  force_collide_pair<OP, SIGMA>(f, p, P, r, OP);
+  force_pair<SIGMA>(p, P, Fx, Fy, Fz, dS4);
+  }
+  V2 f[19];
+  pull_pair<S>(g_in, (unsigned)P.n, nb, px, f);
+  collide_pair<OP>(f, Fx, Fy, Fz, dS4, P, r, OP);
 #pragma unroll
   for (int a = 0; a < 19; ++a) PairIO<S>::st2(g_out + (size_t)a * P.n + nb.self, a, f[a]);
 }

@@ -94,20 +94,36 @@ __device__ __forceinline__ float2 psi_pair(V2 drho, const KParams &P, unsigned &
   return make_float2(out[0], out[1]);
 }
 
-// Force (Eq. 15, with the Eq. 16 term when SIGMA) and collision of both nodes,
-// from p[a] = psi(x + e_a).  OP is kOrth, kNonOrth or 2 (then op_rt picks).
-template <int OP, bool SIGMA>
-__device__ __forceinline__ void force_collide_pair(V2 f[19], const V2 p[19], const KParams &P, const Rates<V2> &r,
-                                                   int op_rt) {
+// Force of both nodes (Eq. 15) and the Eq. 16 term (when SIGMA) from
+// p[a] = psi(x + e_a).
+template <bool SIGMA>
+__device__ __forceinline__ void force_pair(const V2 p[19], const KParams &P, V2 &Fx, V2 &Fy, V2 &Fz, V2 &dS4) {
   V2 Sx, Sy, Sz;
   psi_gradient<V2>(p, Sx, Sy, Sz);
   const V2 kk = V2((double)-P.fG) * p[0];
-  const V2 dS4 = SIGMA ? V2(V2((double)P.fsigma_coef) * V2(Sx * Sx + Sy * Sy + Sz * Sz)) : V2(0.0);
-  const V2 Fx = kk * Sx, Fy = kk * Sy, Fz = kk * Sz;
+  dS4 = SIGMA ? V2(V2((double)P.fsigma_coef) * V2(Sx * Sx + Sy * Sy + Sz * Sz)) : V2(0.0);
+  Fx = kk * Sx;
+  Fy = kk * Sy;
+  Fz = kk * Sz;
+}
+
+// Collision of both nodes with a given force.  OP is kOrth, kNonOrth or 2 (then op_rt picks).
+template <int OP>
+__device__ __forceinline__ void collide_pair(V2 f[19], V2 Fx, V2 Fy, V2 Fz, V2 dS4, const KParams &P,
+                                             const Rates<V2> &r, int op_rt) {
   if (OP == kNonOrth || (OP == 2 && op_rt == kNonOrth))
     collide_nonorth<V2>(f, V2((double)P.frho_ref), Fx, Fy, Fz, dS4, r);
   else
     collide_orth<V2>(f, V2((double)P.frho_ref), Fx, Fy, Fz, dS4, r);
+}
+
+// Both of the above.
+template <int OP, bool SIGMA>
+__device__ __forceinline__ void force_collide_pair(V2 f[19], const V2 p[19], const KParams &P, const Rates<V2> &r,
+                                                   int op_rt) {
+  V2 Fx, Fy, Fz, dS4;
+  force_pair<SIGMA>(p, P, Fx, Fy, Fz, dS4);
+  collide_pair<OP>(f, Fx, Fy, Fz, dS4, P, r, op_rt);
 }
 
 }  // namespace lbm
