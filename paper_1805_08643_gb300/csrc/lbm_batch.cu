@@ -135,12 +135,15 @@ lbm_status rebuild(lbm_batch *b) {
   for (auto &o : order) pair = pair && b->boxes[o.second].d.P.nx % 2 == 0;
   b->pair = pair;
   if (b->nitems) {
-    // resident blocks the kernels are sized for
-    const int per_sm = pair ? (b->tile == lbm::kTile32x4 ? 8 : 4) : (b->tile == lbm::kTile32x4 ? 4 : 2);
+    // resident blocks per SM: the pair kernels' own occupancy (the psi kernel needs half the fused kernel's
+    // registers), the single-pass kernel's launch bounds
+    int pair_per_sm[2] = {1, 1};
+    if (pair) BCK(lbm::batch_pair_occupancy(b->precision, b->eos, b->tile, pair_per_sm), "pair kernel occupancy");
+    const int per_sm = b->tile == lbm::kTile32x4 ? 4 : 2;
     const int grid = std::min(b->grid_blocks * per_sm, b->nitems);
     auto step = [&](int parity) {
       return pair ? lbm::launch_batch_pair(b->precision, b->eos, b->tile, b->d_boxes, b->d_items, b->nitems, parity,
-                                           grid, b->d_err, b->stream)
+                                           b->grid_blocks, pair_per_sm, b->d_err, b->stream)
                   : lbm::launch_batch_onepass(b->precision, b->eos, b->tile, b->d_boxes, b->d_items, b->nitems,
                                               parity, grid, b->d_err, b->stream);
     };

@@ -131,9 +131,13 @@ struct BatchBox {
 // Persistent single-pass launch over the work items (box, tx | ty << 16, z0, z1)
 // of many boxes; grid = number of thread blocks.  FP32 arithmetic forms only.
 // The batch's two-pass step on the pair kernels (every box with an even Nx):
-// the fused pass, then the psi pass of the new level, for one parity.
+// the fused pass, then the psi pass of the new level, for one parity.  Each is
+// a persistent grid of sms x per_sm[k] blocks (at most one per item), per_sm
+// as batch_pair_occupancy gives it: resident blocks per SM of the fused (0)
+// and psi (1) kernels.
+cudaError_t batch_pair_occupancy(int precision, int eos, int tile, int per_sm[2]);
 cudaError_t launch_batch_pair(int precision, int eos, int tile, const BatchBox *boxes, const int4 *items, int nitems,
-                              int parity, int grid, unsigned *err, cudaStream_t s);
+                              int parity, int sms, const int per_sm[2], unsigned *err, cudaStream_t s);
 cudaError_t launch_batch_onepass(int precision, int eos, int tile, const BatchBox *boxes, const int4 *items,
                                  int nitems, int parity, int grid, unsigned *err, cudaStream_t s);
 // Block shape of a tile choice: returns threads per block, sets bx, by.

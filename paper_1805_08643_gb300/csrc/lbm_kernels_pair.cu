@@ -12,6 +12,8 @@
 // instruction issues the work of two nodes.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 #include "lbm_pair.cuh"
@@ -172,38 +174,61 @@ __global__ void __launch_bounds__(TXP *TY) batch_pair_kernel(const BatchBox *__r
   if (e) atomicOr(err, e);
 }
 
+// The fused and psi kernels of one step for a storage type and tile shape;
+// with query set, per_sm receives their resident blocks per SM instead.
 template <typename S, int TXP, int TY>
-cudaError_t batch_pair_shape(int eos, const BatchBox *boxes, const int4 *items, int nitems, int parity, int grid,
-                             unsigned *err, cudaStream_t s) {
-  const dim3 block(TXP, TY);
-  batch_pair_kernel<S, false, kEosNone, TXP, TY><<<grid, block, 0, s>>>(boxes, items, nitems, parity, err);
+cudaError_t batch_pair_shape(int eos, const BatchBox *boxes, const int4 *items, int nitems, int parity, int sms,
+                             int per_sm[2], bool query, unsigned *err, cudaStream_t s) {
+  using K = void (*)(const BatchBox *, const int4 *, int, int, unsigned *);
+  K k[2] = {batch_pair_kernel<S, false, kEosNone, TXP, TY>, nullptr};
   switch (eos) {
-    case kEosCS: batch_pair_kernel<S, true, kEosCS, TXP, TY><<<grid, block, 0, s>>>(boxes, items, nitems, parity, err); break;
-    case kEosExp: batch_pair_kernel<S, true, kEosExp, TXP, TY><<<grid, block, 0, s>>>(boxes, items, nitems, parity, err); break;
-    default: batch_pair_kernel<S, true, kEosNone, TXP, TY><<<grid, block, 0, s>>>(boxes, items, nitems, parity, err); break;
+    case kEosCS: k[1] = batch_pair_kernel<S, true, kEosCS, TXP, TY>; break;
+    case kEosExp: k[1] = batch_pair_kernel<S, true, kEosExp, TXP, TY>; break;
+    default: k[1] = batch_pair_kernel<S, true, kEosNone, TXP, TY>; break;
   }
-  return cudaGetLastError();
+  for (int i = 0; i < 2; ++i) {
+    cudaError_t e;
+    if (query) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[i], k[i], TXP * TY, 0);
+    } else {
+      const int grid = std::max(1, std::min(sms * std::max(per_sm[i], 1), nitems));
+      k[i]<<<grid, dim3(TXP, TY), 0, s>>>(boxes, items, nitems, parity, err);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <typename S>
 cudaError_t batch_pair_tile(int tile, int eos, const BatchBox *boxes, const int4 *items, int nitems, int parity,
-                            int grid, unsigned *err, cudaStream_t s) {
+                            int sms, int per_sm[2], bool query, unsigned *err, cudaStream_t s) {
   switch (tile) {
-    case kTile32x4: return batch_pair_shape<S, 16, 4>(eos, boxes, items, nitems, parity, grid, err, s);
-    case kTile64x4: return batch_pair_shape<S, 32, 4>(eos, boxes, items, nitems, parity, grid, err, s);
-    default: return batch_pair_shape<S, 16, 8>(eos, boxes, items, nitems, parity, grid, err, s);
+    case kTile32x4: return batch_pair_shape<S, 16, 4>(eos, boxes, items, nitems, parity, sms, per_sm, query, err, s);
+    case kTile64x4: return batch_pair_shape<S, 32, 4>(eos, boxes, items, nitems, parity, sms, per_sm, query, err, s);
+    default: return batch_pair_shape<S, 16, 8>(eos, boxes, items, nitems, parity, sms, per_sm, query, err, s);
   }
+}
+
+cudaError_t batch_pair_dispatch(int precision, int tile, int eos, const BatchBox *boxes, const int4 *items, int nitems,
+                                int parity, int sms, int per_sm[2], bool query, unsigned *err, cudaStream_t s) {
+  if (precision == kF32) return batch_pair_tile<float>(tile, eos, boxes, items, nitems, parity, sms, per_sm, query, err, s);
+  if (precision == kF16) return batch_pair_tile<__half>(tile, eos, boxes, items, nitems, parity, sms, per_sm, query, err, s);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
 bool pair_supported(const KParams &P, int precision) { return precision != kF64 && P.nx % 2 == 0; }
 
+cudaError_t batch_pair_occupancy(int precision, int eos, int tile, int per_sm[2]) {
+  return batch_pair_dispatch(precision, tile, eos, nullptr, nullptr, 0, 0, 0, per_sm, true, nullptr, 0);
+}
+
 cudaError_t launch_batch_pair(int precision, int eos, int tile, const BatchBox *boxes, const int4 *items, int nitems,
-                              int parity, int grid, unsigned *err, cudaStream_t s) {
-  if (precision == kF32) return batch_pair_tile<float>(tile, eos, boxes, items, nitems, parity, grid, err, s);
-  if (precision == kF16) return batch_pair_tile<__half>(tile, eos, boxes, items, nitems, parity, grid, err, s);
-  return cudaErrorInvalidValue;
+                              int parity, int sms, const int per_sm[2], unsigned *err, cudaStream_t s) {
+  int ps[2] = {per_sm[0], per_sm[1]};
+  return batch_pair_dispatch(precision, tile, eos, boxes, items, nitems, parity, sms, ps, false, err, s);
 }
 
 cudaError_t launch_psi_pair(const KParams &P, int precision, const void *g, void *psi, unsigned *err,
