@@ -14,4 +14,8 @@ invariants, Maxwell values the paper prints).  One reading stays unpinned
 beyond physics-level agreement: the exact equilibria and forcing moments the
 authors used for the *orthogonal* operator, which the paper does not print
 (``lbm_oracle.meq_orth`` / ``forcing_orth``; see the module docstring).
+
+``d3q15`` restates the D3Q15 non-orthogonal variant the paper says can be
+built the same way (Sec. II A) but does not print; its readings are listed in
+that module's docstring and pinned in ``tests/test_oracle_d3q15.py``.
 """
