@@ -55,6 +55,9 @@ W_HEADLINE = 3.0                # the a = 1 droplet of the 256^3 throughput box
 FUSED_BYTES = {"f64": 19 * 8 * 2 + 8, "f32": 19 * 4 * 2 + 4, "f16": 19 * 2 * 2 + 4}
 # ... and of the psi pass: 19 populations read + psi written
 PSI_BYTES = {"f64": 19 * 8 + 8, "f32": 19 * 4 + 4, "f16": 19 * 2 + 4}
+# the same for the D3Q15 variant (15 populations per node)
+FUSED_BYTES_Q15 = {"f64": 15 * 8 * 2 + 8, "f32": 15 * 4 * 2 + 4, "f16": 15 * 2 * 2 + 4}
+PSI_BYTES_Q15 = {"f64": 15 * 8 + 8, "f32": 15 * 4 + 4, "f16": 15 * 2 + 4}
 HEADLINE = ("nonorth", "f32")
 # DRAM bytes per node of the fused pass, from one ncu capture of the current kernel at 256^3 (dram__bytes_read
 # + dram__bytes_write over the nodes); null for forms without such a capture.
@@ -556,6 +559,18 @@ def main():
                     "status": fst,
                 }
 
+        for fprec in ("f64", "f32", "f16"):
+            steps_f = max(10, args.steps // (8 if fprec == "f64" else 1))
+            fms, fkt, _, fst = time_form("nonorth_d3q15", fprec, args.edge, steps_f, args.warmup, world)
+            f_fused = fkt["fused_ms"] / max(fkt["fused_launches"], 1)
+            f_psi = fkt["psi_ms"] / max(fkt["psi_launches"], 1)
+            fb, pb = FUSED_BYTES_Q15[fprec], PSI_BYTES_Q15[fprec]
+            forms[f"nonorth_d3q15_{fprec}_droplet"] = {
+                "mlups": n * steps_f / (fms / 1e3) / 1e6, "ms_per_step": fms / steps_f, "fused_ms": f_fused,
+                "psi_ms": f_psi, "fused_gbs": fb * n / (f_fused / 1e3) / 1e9,
+                "hbm_frac_fused": fb * n / (f_fused / 1e3) / 1e9 / hbm_peak,
+                "step_gbs": (fb + pb) * n / (fms / steps_f / 1e3) / 1e9, "bytes_per_lup_two_pass": fb + pb,
+                "status": fst, "note": "D3Q15 non-orthogonal variant (one-node kernels)"}
         for fprec in ("f32", "f16"):
             fms, fkt, _, fst = time_form("nonorth", fprec, args.edge, args.steps, args.warmup, world,
                                          eos_arith="f32x2")

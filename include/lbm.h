@@ -12,14 +12,18 @@
  *   f_a(x + e_a, t + 1) = f*_a(x, t), periodic box         (Eq. 5)
  *
  * for the non-orthogonal transformation matrix of Eq. 12 or the usual orthogonal
- * D3Q19 matrix (d'Humieres et al., the paper's Ref. 11).
+ * D3Q19 matrix (d'Humieres et al., the paper's Ref. 11), and for the D3Q15
+ * non-orthogonal variant the paper says follows the same construction
+ * (Sec. II A; see LBM_OP_NONORTHOGONAL_D3Q15).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
  *  - Lattice units: dt = dx = c = 1, c_s^2 = 1/3.
  *  - Node index i = x + Nx*(y + Ny*z), x fastest; N = Nx*Ny*Nz.
- *  - Direction a = 0..18 in the order of Eq. 2.  Population arrays are
- *    structure-of-arrays: element (a, i) at offset a*N + i.
+ *  - Direction a = 0..Q-1, Q = 19 in the order of Eq. 2 (Q = 15 for the D3Q15
+ *    operator: rest, +-x, +-y, +-z as in Eq. 2, then the corners (+,+,+)
+ *    (-,-,-) (+,+,-) (-,-,+) (+,-,+) (-,+,-) (-,+,+) (+,-,-)).  Population
+ *    arrays are structure-of-arrays: element (a, i) at offset a*N + i.
  *  - Every value crossing this boundary is a double, whatever the storage
  *    precision, except device buffers handed to lbm_bind.
  *  - "on_device" = 1: the pointer is CUDA device memory of the context's
@@ -52,8 +56,22 @@ typedef enum {
   LBM_ERR_STATE = 7       /* call out of order (e.g. lbm_step before an init)     */
 } lbm_status;
 
-/* Transformation matrix: the usual orthogonal one, or Eq. 12 (Sec. II B). */
-typedef enum { LBM_OP_ORTHOGONAL = 0, LBM_OP_NONORTHOGONAL = 1 } lbm_operator;
+/* Transformation matrix: the usual orthogonal one, or Eq. 12 (Sec. II B), both
+ * on D3Q19; or the non-orthogonal construction on D3Q15 (Sec. II A says it
+ * follows the same way; the paper prints none).  D3Q15 reading: the Eq. 7-10
+ * monomials on the 15 velocities (1, e_x, e_y, e_z, |e|^2, 3e_x^2 - |e|^2,
+ * e_y^2 - e_z^2, e_x e_y, e_x e_z, e_y e_z, e_x^2 e_y, e_x e_y^2, e_x^2 e_z,
+ * e_x e_y e_z, e_x^2 e_y^2), equilibria and forcing moments of Eqs. 13-14 taken
+ * from the D3Q19 rows each vector equals (their mean where several coincide;
+ * zero for e_x e_y e_z), rates 1, s_e, s_nu x5, s_q x4, s_pi, and Eq. 15 weights
+ * 1/3 (axes), 1/24 (corners).  A D3Q15 context runs the two-pass one-node
+ * kernels in every precision; the single-pass variants (lbm_set_tuning), the
+ * no-alloc step (lbm_step_static) and batches are D3Q19 only. */
+typedef enum {
+  LBM_OP_ORTHOGONAL = 0,
+  LBM_OP_NONORTHOGONAL = 1,
+  LBM_OP_NONORTHOGONAL_D3Q15 = 2
+} lbm_operator;
 
 /* Pseudopotential (Sec. II B): square root of the Carnahan-Starling EOS
  * (Eq. 58), exponential psi0*exp(-rho0/rho), or none (no interaction force). */
@@ -92,8 +110,9 @@ lbm_status lbm_create(const int grid[3], const lbm_eos *eos, double G,
                       void *cuda_stream, lbm_ctx **out);
 
 /* Bytes of the three device buffers a context needs: each of the two
- * population buffers, the psi buffer (two time levels of psi), and the scratch
- * buffer (reductions and the error word). */
+ * population buffers (Q N stored values, and never less than 4N doubles: the
+ * spare one stages rho and u for lbm_moments), the psi buffer (two time levels
+ * of psi), and the scratch buffer (reductions and the error word). */
 lbm_status lbm_buffer_bytes(const lbm_ctx *ctx, size_t *population_bytes,
                             size_t *psi_bytes, size_t *scratch_bytes);
 
@@ -133,8 +152,9 @@ lbm_status lbm_step(lbm_ctx *ctx, int n);
  * u_z) of the current state, Eq. 6 with the force of Eq. 15. */
 lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u, int on_device);
 
-/* The post-streaming populations f_a(x, t) of the current time t (19N doubles,
- * SoA), and the reverse: make them the current state (keeps rho_ref). */
+/* The post-streaming populations f_a(x, t) of the current time t (QN doubles,
+ * SoA; Q = 19, or 15 for LBM_OP_NONORTHOGONAL_D3Q15), and the reverse: make
+ * them the current state (keeps rho_ref). */
 lbm_status lbm_get_populations(lbm_ctx *ctx, double *f, int on_device);
 lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
 
@@ -175,8 +195,9 @@ lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
  * per 64x4 tile and plane), freed by lbm_destroy.  tile picks the x-y tile of
  * the single-pass kernel (0: 32x4, 1: 32x8, 2: 64x4); z_planes the z planes
  * each thread block marches through (0 = automatic).  Results do not depend on
- * tile or z_planes.  Errors: LBM_ERR_ARG (bad value, or a mode the context's
- * precision or Nx does not support); LBM_ERR_OOM / LBM_ERR_CUDA (mode 4's flag
+ * tile or z_planes.  Errors: LBM_ERR_ARG (bad value, a mode the context's
+ * precision or Nx does not support, or a single-pass mode on a D3Q15 context);
+ * LBM_ERR_OOM / LBM_ERR_CUDA (mode 4's flag
  * array could not be allocated). */
 lbm_status lbm_set_tuning(lbm_ctx *ctx, int single_pass, int tile, int z_planes);
 
@@ -217,7 +238,8 @@ long long lbm_step_count(const lbm_ctx *ctx);
  *    (cudaGetSymbolAddress); make that first call before any stream capture.
  *  - Asynchronous on the context's stream.  A density outside the EOS domain
  *    gives NaN populations in f_out (there is no error word on this path).
- * Errors: LBM_ERR_ARG (null or aliased pointers, precision, size), LBM_ERR_CUDA. */
+ * Errors: LBM_ERR_ARG (null or aliased pointers, precision, size, a D3Q15 context),
+ * LBM_ERR_CUDA. */
 lbm_status lbm_step_static(const lbm_ctx *ctx, const double *f_in, double *f_out);
 
 /* ------------------------------------------------------------------ batches
@@ -246,8 +268,9 @@ size_t lbm_batch_box_bytes(int precision, const int grid[3]);
 lbm_status lbm_batch_create(int precision, int eos_kind, size_t hbm_budget_bytes, void *cuda_stream,
                             lbm_batch **out);
 
-/* Add a box (parameters as in lbm_create); *id receives its handle.  Errors:
- * LBM_ERR_ARG, LBM_ERR_OOM when the budget or the device has no room. */
+/* Add a box (parameters as in lbm_create; D3Q19 operators only); *id receives
+ * its handle.  Errors: LBM_ERR_ARG, LBM_ERR_OOM when the budget or the device
+ * has no room. */
 lbm_status lbm_batch_add(lbm_batch *b, const int grid[3], const lbm_eos *eos, double G, const lbm_rates *rates,
                          int op, double sigma, int *id);
 lbm_status lbm_batch_remove(lbm_batch *b, int id);

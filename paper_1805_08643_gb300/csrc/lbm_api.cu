@@ -69,7 +69,11 @@ lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *where) {
     if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
   } while (0)
 
-size_t pop_bytes(const lbm_ctx *c) { return (size_t)19 * c->P.n * lbm::storage_bytes(c->precision); }
+// A population buffer holds Q N stored values, and at least 4N doubles: the
+// spare one stages rho and u for lbm_moments (D3Q15 with FP16 storage is 30N bytes).
+size_t pop_bytes(const lbm_ctx *c) {
+  return std::max((size_t)c->P.q * c->P.n * lbm::storage_bytes(c->precision), (size_t)4 * c->P.n * sizeof(double));
+}
 size_t psi_bytes(const lbm_ctx *c) { return 2 * (size_t)c->P.n * lbm::psi_elem_bytes(c->precision); }
 void *psi_at(lbm_ctx *c, int level) {
   return (char *)c->psi + (size_t)level * c->P.n * lbm::psi_elem_bytes(c->precision);
@@ -387,11 +391,11 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f, int on_device) {
   if (!c->initialized) return fail(c, LBM_ERR_STATE, "no state");
   const size_t n = c->P.n;
   if (on_device) {
-    CK(lbm::launch_get_populations(c->P, c->precision, c->g[c->cur], f, 0, 19, c->L), "get_populations kernel");
+    CK(lbm::launch_get_populations(c->P, c->precision, c->g[c->cur], f, 0, c->P.q, c->L), "get_populations kernel");
     return LBM_OK;
   }
   double *tmp = (double *)spare(c);
-  for (int a = 0; a < 19; ++a) {
+  for (int a = 0; a < c->P.q; ++a) {
     CK(lbm::launch_get_populations(c->P, c->precision, c->g[c->cur], tmp, a, a + 1, c->L),
        "get_populations kernel");
     CK(cudaMemcpyAsync(f + a * n, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, c->L.stream), "D2H f");
@@ -405,10 +409,10 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f, int on_device) {
   if (!c->initialized) return fail(c, LBM_ERR_STATE, "set_populations needs an init (for rho_ref)");
   const size_t n = c->P.n;
   if (on_device) {
-    CK(lbm::launch_set_populations(c->P, c->precision, f, c->g[c->cur], 0, 19, c->L), "set_populations kernel");
+    CK(lbm::launch_set_populations(c->P, c->precision, f, c->g[c->cur], 0, c->P.q, c->L), "set_populations kernel");
   } else {
     double *tmp = (double *)spare(c);
-    for (int a = 0; a < 19; ++a) {
+    for (int a = 0; a < c->P.q; ++a) {
       CK(cudaMemcpyAsync(tmp, f + a * n, sizeof(double) * n, cudaMemcpyHostToDevice, c->L.stream), "H2D f");
       CK(lbm::launch_set_populations(c->P, c->precision, tmp, c->g[c->cur], a, a + 1, c->L),
          "set_populations kernel");
@@ -467,6 +471,7 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
   if (!c || single_pass < 0 || single_pass > 4 || tile < 0 || tile > 2 || z_planes < 0)
     return fail(c, LBM_ERR_ARG, "bad tuning");
   if (single_pass && c->precision == LBM_F64) return fail(c, LBM_ERR_ARG, "single pass needs FP32 arithmetic");
+  if (single_pass && c->P.q == 15) return fail(c, LBM_ERR_ARG, "the single-pass variants are D3Q19 kernels");
   if (single_pass == 2 && !lbm::onepass_tma_supported(c->P, c->precision))
     return fail(c, LBM_ERR_ARG, "bulk-copy single pass needs FP32 storage, Nx % 4 == 0 and Nx >= 40");
   if (single_pass == 3 && !lbm::onchip_supported(c->P, c->precision))
@@ -571,7 +576,7 @@ bool fill_params(const int grid[3], const lbm_eos *eos, double G, const lbm_rate
   const long long n = (long long)grid[0] * grid[1] * grid[2];
   // 32-bit node index, unsigned 32-bit element offsets (19 N < 2^32), grid.z limit
   if (n >= (1LL << 31) || 19 * n >= (1LL << 32) || grid[2] > 65535) return false;
-  if (op != LBM_OP_ORTHOGONAL && op != LBM_OP_NONORTHOGONAL) return false;
+  if (op != LBM_OP_ORTHOGONAL && op != LBM_OP_NONORTHOGONAL && op != LBM_OP_NONORTHOGONAL_D3Q15) return false;
   if (precision < LBM_F64 || precision > LBM_F32_STORE_F16) return false;
   if (eos->kind < LBM_EOS_CS || eos->kind > LBM_EOS_NONE) return false;
   const double rs[6] = {rates->s_e, rates->s_nu, rates->s_q, rates->s_pi, rates->s_eps, rates->s_m};
@@ -591,6 +596,7 @@ bool fill_params(const int grid[3], const lbm_eos *eos, double G, const lbm_rate
   P.ny = grid[1];
   P.nz = grid[2];
   P.n = (int)n;
+  P.q = op == LBM_OP_NONORTHOGONAL_D3Q15 ? 15 : 19;
   P.G = eos->kind == LBM_EOS_NONE ? 0.0 : G;
   P.rho_ref = 0.0;
   P.s_e = rates->s_e;

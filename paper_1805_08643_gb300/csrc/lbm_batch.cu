@@ -245,6 +245,7 @@ lbm_status lbm_batch_add(lbm_batch *b, const int grid[3], const lbm_eos *eos, do
   if (!b || !id) return LBM_ERR_ARG;
   if (!eos || eos->kind != b->eos) return bfail(b, LBM_ERR_ARG, "every box of a batch uses the batch's EOS kind");
   KParams P;
+  if (op == LBM_OP_NONORTHOGONAL_D3Q15) return bfail(b, LBM_ERR_ARG, "batches hold D3Q19 boxes");
   if (!lbm::fill_params(grid, eos, G, rates, op, b->precision, sigma, &P)) return bfail(b, LBM_ERR_ARG, "bad box");
   const size_t bytes = box_bytes(b->precision, P.n);
   if (b->used + bytes > b->budget) return bfail(b, LBM_ERR_OOM, "HBM budget of the batch exceeded");

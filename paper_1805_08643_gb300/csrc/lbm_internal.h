@@ -8,7 +8,7 @@
 namespace lbm {
 
 enum Precision { kF64 = 0, kF32 = 1, kF16 = 2 };
-enum Operator { kOrth = 0, kNonOrth = 1 };
+enum Operator { kOrth = 0, kNonOrth = 1, kNonOrthQ15 = 2 };
 enum EosKind { kEosCS = 0, kEosExp = 1, kEosNone = 2 };
 
 // Error bits the kernels set in the device error word.
@@ -18,6 +18,7 @@ enum : unsigned { kErrEosDomain = 1u, kErrNonFinite = 2u, kErrTimeout = 4u };
 struct KParams {
   int nx, ny, nz;
   int n;             // nx * ny * nz (< 2^31)
+  int q;             // lattice: 19 (D3Q19, both operators) or 15 (D3Q15 non-orthogonal)
   double G;          // interaction strength, Eq. 15
   double rho_ref;    // reference density of the deviation storage
   // relaxation rates (see lbm_rates in lbm.h)

@@ -219,7 +219,7 @@ cudaError_t batch_pair_dispatch(int precision, int tile, int eos, const BatchBox
 
 }  // namespace
 
-bool pair_supported(const KParams &P, int precision) { return precision != kF64 && P.nx % 2 == 0; }
+bool pair_supported(const KParams &P, int precision) { return P.q == 19 && precision != kF64 && P.nx % 2 == 0; }
 
 cudaError_t batch_pair_occupancy(int precision, int eos, int tile, int per_sm[2]) {
   return batch_pair_dispatch(precision, tile, eos, nullptr, nullptr, 0, 0, 0, per_sm, true, nullptr, 0);

@@ -96,6 +96,7 @@ extern "C" lbm_status lbm_step_static(const lbm_ctx *ctx, const double *f_in, do
   cudaStream_t stream = nullptr;
   if (!lbm::ctx_params(ctx, &P, &precision, &op, &sigma_on, &stream)) return LBM_ERR_ARG;
   if (precision != LBM_F64) return LBM_ERR_ARG;                 // FP64 populations only
+  if (P.q != 19) return LBM_ERR_ARG;                            // D3Q19 kernels only
   if ((long long)P.n > LBM_STATIC_MAX_NODES) return LBM_ERR_ARG;  // beyond the static psi array
   P.rho_ref = 0.0;  // f_in / f_out hold absolute populations
   double *psi = nullptr;

@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblbm.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_EOS_DOMAIN, ERR_TIMEOUT, ERR_STATE = range(8)
-OPERATORS = {"orth": 0, "nonorth": 1}
+OPERATORS = {"orth": 0, "nonorth": 1, "nonorth_d3q15": 2}
+LATTICE_Q = {"orth": 19, "nonorth": 19, "nonorth_d3q15": 15}
 PRECISIONS = {"f64": 0, "f32": 1, "f16": 2}
 EOS_KINDS = {"cs": 0, "exp": 1, "none": 2}
 
@@ -125,7 +126,9 @@ def _ptr(a: np.ndarray):
 
 
 class Lattice:
-    """One periodic D3Q19 box on the current CUDA device.
+    """One periodic box on the current CUDA device: D3Q19 with the orthogonal or
+    non-orthogonal operator, or the D3Q15 non-orthogonal variant
+    (``operator="nonorth_d3q15"``).
 
     Device buffers come from PyTorch and are bound to the C context; work runs
     on the current torch stream (or ``stream``, a torch.cuda.Stream).
@@ -139,6 +142,7 @@ class Lattice:
         self.grid = tuple(int(v) for v in grid)
         self.n = self.grid[0] * self.grid[1] * self.grid[2]
         self.operator, self.precision = operator, precision
+        self.q = LATTICE_Q[operator]
         rates = rates or Rates()
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         eos_s = LbmEos(EOS_KINDS[eos], a, b, R, T, psi0, rho0)
@@ -237,13 +241,13 @@ class Lattice:
 
     def populations(self):
         nx, ny, nz = self.grid
-        f = np.empty(19 * self.n)
+        f = np.empty(self.q * self.n)
         self._check(lib.lbm_get_populations(self._h, _ptr(f), 0), "lbm_get_populations")
-        return f.reshape(19, nz, ny, nx)
+        return f.reshape(self.q, nz, ny, nx)
 
     def set_populations(self, f):
         a = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
-        assert a.size == 19 * self.n
+        assert a.size == self.q * self.n
         self._check(lib.lbm_set_populations(self._h, _ptr(a), 0), "lbm_set_populations")
 
     def diag(self):

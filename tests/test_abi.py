@@ -94,3 +94,26 @@ def test_set_tuning_validates_modes_without_touching_the_gpu(lbm):
     assert lbm.lib.lbm_get_tuning(h, ctypes.byref(sp), ctypes.byref(t), ctypes.byref(z)) == lbm.OK
     assert (sp.value, t.value, z.value) == (1, 2, 16)
     lbm.lib.lbm_destroy(h)
+
+
+def test_d3q15_contexts_size_their_buffers_and_reject_d3q19_only_paths(lbm):
+    st, h = _create(lbm, op=2)  # LBM_OP_NONORTHOGONAL_D3Q15, FP64
+    assert st == lbm.OK
+    pb, sb, xb = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+    assert lbm.lib.lbm_buffer_bytes(h, ctypes.byref(pb), ctypes.byref(sb), ctypes.byref(xb)) == lbm.OK
+    assert pb.value == 15 * 512 * 8 and sb.value == 2 * 512 * 8
+    buf = ctypes.c_void_p(1 << 20)  # never dereferenced: the argument check comes first
+    assert lbm.lib.lbm_step_static(h, buf, ctypes.c_void_p(2 << 20)) == lbm.ERR_ARG
+    lbm.lib.lbm_destroy(h)
+    st, h = _create(lbm, op=2, prec=1)
+    assert st == lbm.OK
+    for mode in (1, 2, 3, 4):
+        assert lbm.lib.lbm_set_tuning(h, mode, 1, 0) == lbm.ERR_ARG
+    assert b"D3Q19" in lbm.lib.lbm_last_error(h)
+    assert lbm.lib.lbm_set_tuning(h, 0, 1, 0) == lbm.OK
+    lbm.lib.lbm_destroy(h)
+    st, h = _create(lbm, op=2, prec=2)
+    lbm.lib.lbm_buffer_bytes(h, ctypes.byref(pb), ctypes.byref(sb), ctypes.byref(xb))
+    assert pb.value == 4 * 512 * 8  # 15 halves per node are less than the 4 doubles lbm_moments stages
+    lbm.lib.lbm_destroy(h)
+    assert _create(lbm, op=3)[0] == lbm.ERR_ARG

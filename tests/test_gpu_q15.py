@@ -1,0 +1,246 @@
+"""Parity of the D3Q15 non-orthogonal variant (CUDA path through the C ABI) with
+the FP64 D3Q15 oracle.
+
+Gates as for D3Q19: FP64 max |d rho|, |d u| <= 1e-11 after 200 steps (32^3
+droplet, non-cubic and odd-Nx boxes); FP32 / FP16 storage within the bounds
+derived in test_gpu_precision (2e-5 / 2e-3: the D3Q15 density sums 15 stored
+values instead of 19, so the same bounds hold with more margin); sampled
+one-step parity at 256^3 in the configuration the benchmark times.
+"""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import coexistence, droplet_rho, lattice, max_abs, physics
+from oracle import d3q15 as D
+from oracle import lbm_oracle as L
+
+pytestmark = pytest.mark.gpu
+
+OP = "nonorth_d3q15"
+TOL_F64 = 1e-11
+TOL = {"f32": 2e-5, "f16": 2e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1805_08643_gb300 import _build
+
+    _build.build()
+
+
+def _params(grid, phys):
+    return L.Params(grid=tuple(grid), operator="nonorth", **phys)
+
+
+def _droplet_case(grid, precision="f64", T_over_Tc=0.8, R=8.0, W=2.0, **phys_kw):
+    phys = physics(T_over_Tc=T_over_Tc, **phys_kw)
+    rl, rv = coexistence(T_over_Tc)
+    centre = tuple(n / 2 for n in grid)
+    lat = lattice(grid, OP, precision, phys)
+    lat.init_droplet(centre, R, W, rl, rv)
+    p = _params(grid, phys)
+    return lat, p, D.equilibrium_state(p, droplet_rho(grid, centre, R, W, rl, rv))
+
+
+def test_initial_state_matches_oracle():
+    lat, p, f0 = _droplet_case((32, 32, 32))
+    assert lat.q == 15
+    rho, u = lat.moments()
+    rho_o, u_o, _, _ = D.macroscopic(p, f0)
+    assert max_abs(rho, rho_o) < 1e-14 and max_abs(u, u_o) < 1e-14
+    assert max_abs(lat.populations(), f0) < 1e-15
+    lat.close()
+
+
+def test_single_step_every_population():
+    grid = (8, 6, 5)
+    phys = physics(sigma=0.1)
+    p = _params(grid, phys)
+    rng = np.random.default_rng(15)
+    rho = rng.uniform(0.05, 0.28, grid[::-1])
+    u = rng.uniform(-0.02, 0.02, (3,) + grid[::-1])
+    f = D.equilibrium_state(p, rho, u) + rng.normal(0, 2e-4, (15,) + grid[::-1])
+    lat = lattice(grid, OP, "f64", phys)
+    lat.init_field(rho, rho_ref=0.02)
+    lat.set_populations(f)
+    assert max_abs(lat.populations(), f) < 1e-16
+    lat.step(1)
+    assert max_abs(lat.populations(), D.step(p, f)) < 1e-15
+    lat.close()
+
+
+@pytest.mark.parametrize("grid", [(32, 32, 32), (24, 20, 28), (25, 20, 28)])
+def test_fp64_parity_after_200_steps(grid):
+    lat, p, f0 = _droplet_case(grid)
+    lat.step(200)
+    assert lat.check() == 0
+    rho, u = lat.moments()
+    rho_o, u_o, _, _ = D.macroscopic(p, D.run(p, f0, 200))
+    err_rho, err_u = max_abs(rho, rho_o), max_abs(u, u_o)
+    print(f"d3q15 {grid}: max|drho|={err_rho:.3e} max|du|={err_u:.3e}")
+    assert err_rho <= TOL_F64 and err_u <= TOL_F64
+    lat.close()
+
+
+def test_sigma_term_and_variable_viscosity_parity():
+    rl, rv = coexistence(0.8)
+    lat, p, f0 = _droplet_case((16, 18, 20), R=5.0, sigma=0.105, other=1.2, s_nu=1.0 / 0.8)
+    lat.set_variable_viscosity(rl, rv, 0.05, 0.25)
+    p = p.with_(nu_l=0.05, nu_v=0.25, rho_l_nu=rl, rho_v_nu=rv)
+    lat.step(50)
+    rho, u = lat.moments()
+    rho_o, u_o, _, _ = D.macroscopic(p, D.run(p, f0, 50))
+    assert max_abs(rho, rho_o) <= TOL_F64 and max_abs(u, u_o) <= TOL_F64
+    lat.close()
+
+
+def test_exponential_pseudopotential_parity():
+    from oracle import maxwell
+
+    grid = (16, 16, 16)
+    phys = physics(eos="exp", G=-10.0 / 3.0, other=1.2)
+    phys["s_e"] = 0.8
+    p = _params(grid, phys).with_(psi0=1.0, rho0=1.0)
+    rl, rv = maxwell.coexistence_exp()
+    rho0 = droplet_rho(grid, (8, 8, 8), 5.0, 3.0, rl, rv)
+    lat = lattice(grid, OP, "f64", phys)
+    lat.init_field(rho0, rho_ref=rv)
+    lat.step(50)
+    rho, u = lat.moments()
+    rho_o, u_o, _, _ = D.macroscopic(p, D.run(p, D.equilibrium_state(p, rho0), 50))
+    assert max_abs(rho, rho_o) <= TOL_F64 and max_abs(u, u_o) <= TOL_F64
+    lat.close()
+
+
+def test_flat_interface_diagnostics_and_conservation():
+    grid = (8, 8, 64)
+    phys = physics(T_over_Tc=0.7, sigma=0.116)
+    rl, rv = coexistence(0.7)
+    lat = lattice(grid, OP, "f64", phys)
+    lat.init_flat(2, 16.0, 48.0, 2.0, rl, rv)
+    p = _params(grid, phys)
+    f0 = D.equilibrium_state(p, L.slab_density(grid, 2, 16.0, 48.0, 2.0, rl, rv))
+    d0 = lat.diag()
+    lat.step(100)
+    d1 = lat.diag()
+    rho, u = lat.moments()
+    rho_o, u_o, _, _ = D.macroscopic(p, D.run(p, f0, 100))
+    assert max_abs(rho, rho_o) <= TOL_F64 and max_abs(u, u_o) <= TOL_F64
+    assert abs(d0["mass"] - D.total_mass(f0)) < 1e-12 * d0["mass"]
+    assert abs(d1["mass"] - d0["mass"]) < 1e-13 * d0["mass"]
+    assert max(abs(m) for m in d1["momentum"]) < 1e-13 * d0["mass"]
+    assert abs(d1["max_u"] - float(np.sqrt((u_o * u_o).sum(0)).max())) < 1e-12
+    lat.close()
+
+
+@pytest.fixture(scope="module")
+def oracle_200():
+    cache = {}
+
+    def get(grid):
+        if grid not in cache:
+            phys = physics(T_over_Tc=0.8)
+            rl, rv = coexistence(0.8)
+            p = _params(grid, phys)
+            f = D.run(p, D.equilibrium_state(p, droplet_rho(grid, tuple(n / 2 for n in grid), 8.0, 2.0, rl, rv)),
+                      200)
+            cache[grid] = D.macroscopic(p, f)[:2]
+        return cache[grid]
+
+    return get
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("grid", [(32, 32, 32), (25, 20, 28)])
+@pytest.mark.parametrize("eos_arith", ["f64", "f32x2"])
+def test_reduced_precision_against_fp64_oracle(oracle_200, prec, grid, eos_arith):
+    rho_o, u_o = oracle_200(grid)
+    lat, _, _ = _droplet_case(grid, precision=prec)
+    if eos_arith != "f64":
+        lat.set_eos_arith(eos_arith)
+    d0 = lat.diag()
+    lat.step(200)
+    d1 = lat.diag()
+    rho, u = lat.moments()
+    assert lat.check() == 0
+    lat.close()
+    err_r, err_u = max_abs(rho, rho_o), max_abs(u, u_o)
+    print(f"d3q15 {prec} {grid} eos {eos_arith}: |drho|={err_r:.2e} |du|={err_u:.2e}")
+    assert err_r <= TOL[prec] and err_u <= TOL[prec]
+    assert abs(d1["mass"] - d0["mass"]) <= 20 * TOL[prec] * d0["mass"] / 15
+
+
+def test_eos_domain_error_is_reported():
+    from paper_1805_08643_gb300.lbm import ERR_EOS_DOMAIN, OK
+
+    grid = (8, 8, 8)
+    lat = lattice(grid, OP, "f32", physics())
+    rho = np.full(grid[::-1], 0.2)
+    rho[3, 3, 3] = 1.2  # b rho / 4 >= 1
+    lat.init_field(rho, rho_ref=0.2)
+    lat.step(1)
+    assert lat.check() == ERR_EOS_DOMAIN and lat.check() == OK
+    lat.close()
+
+
+def test_batches_reject_d3q15_boxes():
+    from paper_1805_08643_gb300.lbm import Batch, LBMError
+
+    b = Batch("f32", "cs", hbm_budget_bytes=1 << 30)
+    with pytest.raises(LBMError):
+        b.add((16, 16, 16), OP, T=0.07)
+    b.close()
+
+
+def _cube(f, x, y, z, n):
+    iz, iy, ix = [(np.arange(c - 3, c + 4) % n) for c in (z, y, x)]
+    return f[np.ix_(np.arange(15), iz, iy, ix)]
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-13), ("f32", 5e-6)])
+def test_sampled_one_step_parity_at_256(prec, tol):
+    n = 256
+    phys = physics(T_over_Tc=0.7, sigma=0.105)
+    rl, rv = coexistence(0.7)
+    lat = lattice((n,) * 3, OP, prec, phys)
+    lat.init_droplet((n / 2,) * 3, 40.0, 3.0, rl, rv)
+    lat.step(20)
+    f_t = lat.populations()
+    lat.step(1)
+    f_t1 = lat.populations()
+    rho, u = lat.moments()
+    assert lat.check() == 0
+    lat.close()
+    p = L.Params(grid=(7, 7, 7), **phys)
+    rng = np.random.default_rng(1805)
+    pts = [(0, 0, 0), (n - 1, n - 1, n - 1), (n // 2, n // 2, n // 2), (n // 2 + 40, n // 2, n // 2),
+           (n // 2, n // 2 - 38, n // 2 + 3)]
+    pts += [tuple(int(v) for v in rng.integers(0, n, 3)) for _ in range(40)]
+    worst = 0.0
+    for (x, y, z) in pts:
+        nxt = D.step(p, _cube(f_t, x, y, z, n))
+        r_o, u_o, _, _ = D.macroscopic(p, nxt)
+        err = max(abs(r_o[3, 3, 3] - rho[z, y, x]), float(np.max(np.abs(u_o[:, 3, 3, 3] - u[:, z, y, x]))),
+                  float(np.max(np.abs(nxt[:, 3, 3, 3] - f_t1[:, z, y, x]))))
+        worst = max(worst, err)
+        assert err <= tol, ((x, y, z), err)
+    print(f"d3q15 {prec} 256^3 sampled one-step parity: worst {worst:.2e}")
+
+
+def test_throughput_box_runs_its_1000_steps():
+    n = 256
+    phys = physics(T_over_Tc=0.7, sigma=0.105)
+    rl, rv = coexistence(0.7)
+    lat = lattice((n,) * 3, OP, "f32", phys)
+    lat.init_droplet((n / 2,) * 3, 40.0, 3.0, rl, rv)
+    d0 = lat.diag()
+    lat.step(1000)
+    d1 = lat.diag()
+    assert lat.check() == 0
+    assert abs(d1["mass"] - d0["mass"]) < 1e-4 * d0["mass"]
+    assert d1["max_u"] < 0.05
+    lat.close()
