@@ -415,6 +415,7 @@ cudaError_t fused_dispatch(const KParams &P, bool sigma, const void *g_in, void 
 cudaError_t launch_psi(const KParams &P, int precision, const void *g, void *psi, unsigned *err,
                        const Launch &L, bool df) {
   if (P.q == 15) {
+    if (pair_supported(P, precision)) return launch_psi_pair(P, precision, g, psi, err, L, df);
     switch (precision) {
       case kF64: return psi_dispatch<kF64, false, 15>(P, g, psi, err, L);
       case kF32:
@@ -437,6 +438,7 @@ cudaError_t launch_psi(const KParams &P, int precision, const void *g, void *psi
 cudaError_t launch_fused(const KParams &P, int precision, int op, bool sigma, const void *g_in, void *g_out,
                          const void *psi, const Launch &L) {
   if (P.q == 15) {
+    if (pair_supported(P, precision)) return launch_fused_pair(P, precision, op, sigma, g_in, g_out, psi, L);
     switch (precision) {
       case kF64: return fused_dispatch<kF64, kNonOrth, 15>(P, sigma, g_in, g_out, psi, L);
       case kF32: return fused_dispatch<kF32, kNonOrth, 15>(P, sigma, g_in, g_out, psi, L);
