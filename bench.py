@@ -406,24 +406,51 @@ def precision_study(edge=512, steps=5000):
             "forms": table}
 
 
-def cpu_baseline(seconds_target=15.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+def lattice_name(op):
+    return "D3Q15" if op == "nonorth_d3q15" else "D3Q19"
+
+
+def workload_text(op, prec, edge):
+    """The headline workload, named by what it is (shared by both arms)."""
+    op_text = {"nonorth": "non-orthogonal", "orth": "orthogonal", "nonorth_d3q15": "non-orthogonal"}[op]
+    return (f"{lattice_name(op)} {op_text} MRT + CS pseudopotential, {edge}^3 periodic box, "
+            f"droplet R={40.0 * edge / 256:g} W={W_HEADLINE:g}, T=0.7Tc, sigma=0.105 (Eq. 16), {PREC_TEXT[prec]}")
+
+
+def oracle_for(op):
+    """The oracle module of the operator's lattice and the operator name its Params take."""
+    if op == "nonorth_d3q15":
+        from oracle import d3q15 as D
+
+        return D, "nonorth"
+    from oracle import lbm_oracle as L
+
+    return L, op
+
+
+def oracle_slab(op, nz):
+    """Oracle state of the nz-plane slab through the centre of the 256^3 droplet box (periodic in z)."""
     from oracle import lbm_oracle as L
     from oracle import maxwell
 
-    nz = 8
-    grid = (EDGE, EDGE, nz)
+    O, oop = oracle_for(op)
     Tc = L.critical_temperature(A, B, R_GAS)
     rl, rv = maxwell.coexistence_cs(T_OVER_TC, A, B, R_GAS)
-    p = L.Params(grid=grid, operator=HEADLINE[0], a=A, b=B, R=R_GAS, T=T_OVER_TC * Tc, G=G,
+    p = L.Params(grid=(EDGE, EDGE, nz), operator=oop, a=A, b=B, R=R_GAS, T=T_OVER_TC * Tc, G=G,
                  sigma=SIGMA_DROPLET, **RATES)
-    # the slab of the 256^3 droplet box through its centre (periodic in z)
     rho = L.droplet_density((EDGE, EDGE, EDGE), (EDGE / 2,) * 3, 40.0, W_HEADLINE, rl, rv)[EDGE // 2 - nz // 2:EDGE // 2 + nz // 2]
-    f = L.equilibrium_state(p, rho)
+    return O, p, O.equilibrium_state(p, rho)
+
+
+def cpu_baseline(op=None, seconds_target=15.0):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
+    op = op or HEADLINE[0]
+    nz = 8
+    O, p, f = oracle_slab(op, nz)
     steps = 0
     t0 = time.perf_counter()
     while True:
-        f = L.step(p, f)
+        f = O.step(p, f)
         steps += 1
         if time.perf_counter() - t0 > seconds_target:
             break
@@ -431,28 +458,19 @@ def cpu_baseline(seconds_target=15.0):
     nodes = EDGE * EDGE * nz
     return {"value": nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{EDGE}x{EDGE}x{nz} slab through the droplet centre, {steps} FP64 steps, "
-                      f"non-orthogonal operator, single-threaded numpy"}
+                      f"{lattice_name(op)} {op} operator, single-threaded numpy"}
 
 
 def reference_arm(args, world, rank):
     if rank != 0:
         return
-    from oracle import lbm_oracle as L
-    from oracle import maxwell
-
     nz = 2  # one step of this slab takes about 50 ms: the default 1000 steps end within a minute
-    grid = (EDGE, EDGE, nz)
-    Tc = L.critical_temperature(A, B, R_GAS)
-    rl, rv = maxwell.coexistence_cs(T_OVER_TC, A, B, R_GAS)
-    p = L.Params(grid=grid, operator=HEADLINE[0], a=A, b=B, R=R_GAS, T=T_OVER_TC * Tc, G=G,
-                 sigma=SIGMA_DROPLET, **RATES)
-    rho = L.droplet_density((EDGE, EDGE, EDGE), (EDGE / 2,) * 3, 40.0, W_HEADLINE, rl, rv)[EDGE // 2 - nz // 2:EDGE // 2 + nz // 2]
-    f = L.equilibrium_state(p, rho)
+    O, p, f = oracle_slab(args.op, nz)
     for _ in range(args.warmup):
-        f = L.step(p, f)
+        f = O.step(p, f)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        f = L.step(p, f)
+        f = O.step(p, f)
     dt = time.perf_counter() - t0
     nodes = EDGE * EDGE * nz
     v = nodes * args.steps / dt / 1e6
@@ -461,8 +479,8 @@ def reference_arm(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": f"D3Q19 nonorth MRT droplet {EDGE}^3 (sampled slab)",
-                                        "edge": EDGE, "T_over_Tc": T_OVER_TC},
+        "data": "synthetic", "config": {"workload": workload_text(args.op, args.prec, EDGE), "edge": EDGE,
+                                        "operator": args.op, "precision": args.prec, "parallelism": "single"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -475,7 +493,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--edge", type=int, default=EDGE)
-    ap.add_argument("--op", default=HEADLINE[0], choices=["nonorth", "orth"])
+    ap.add_argument("--op", default=HEADLINE[0], choices=["nonorth", "orth", "nonorth_d3q15"])
     ap.add_argument("--prec", default=HEADLINE[1], choices=["f64", "f32", "f16"])
     ap.add_argument("--single-pass", type=int, default=0,
                     help="1: single-pass kernel, 2: its bulk-copy variant, 3: on-chip-psi single pass, "
@@ -522,9 +540,10 @@ def main():
     value = sum_over_ranks(n * args.steps / (ms / 1e3) / 1e6, world)  # all ranks' nodes / max time
     fused_ms = kt["fused_ms"] / max(kt["fused_launches"], 1)
     psi_ms = kt["psi_ms"] / max(kt["psi_launches"], 1)
-    achieved = FUSED_BYTES[prec] * n / (fused_ms / 1e3) / 1e9
+    fused_bytes = (FUSED_BYTES_Q15 if op == "nonorth_d3q15" else FUSED_BYTES)[prec]
+    achieved = fused_bytes * n / (fused_ms / 1e3) / 1e9
 
-    if prec == "f64":
+    if prec == "f64" and op in FUSED_FP64_INSTR:
         ach = FUSED_FP64_INSTR[op] * n / (fused_ms / 1e3) / 1e9
         roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GINSTR, "unit": "G FP64 instr/s",
                     "frac": ach / FP64_PEAK_GINSTR, "traffic": None, "peak_kind": "derived: 2 FP64/SM/clk x 152 x 2070 MHz",
@@ -535,7 +554,7 @@ def main():
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                     "frac": achieved / hbm_peak, "traffic": dram * n if dram else None,
                     "peak_kind": peak_kind, "kernel": "single pass" if args.single_pass else "fused force+collide+stream",
-                    "bytes_per_node": FUSED_BYTES[prec], "fused_ms": fused_ms, "psi_ms": psi_ms}
+                    "bytes_per_node": fused_bytes, "fused_ms": fused_ms, "psi_ms": psi_ms}
     forms = {}
     if args.forms == "all":
         for fop in ("nonorth", "orth"):
@@ -603,7 +622,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline()
+        cpu = cpu_baseline(op)
 
     if rank != 0:
         return
@@ -611,12 +630,10 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic",
-        "config": {"workload": f"D3Q19 non-orthogonal MRT + CS pseudopotential, {args.edge}^3 periodic box, "
-                               f"droplet R={40.0 * args.edge / 256:g} W=5, T=0.7Tc, sigma=0.105 (Eq. 16), "
-                               f"{op} operator, {PREC_TEXT[prec]}",
+        "config": {"workload": workload_text(op, prec, args.edge),
                    "edge": args.edge, "operator": op, "precision": prec,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (populations 1.27 GB per buffer)"},
+                   "l2": f"inputs larger than L2 (populations {(15 if op == 'nonorth_d3q15' else 19) * n * {'f64': 8, 'f32': 4, 'f16': 2}[prec] / 1e9:.2f} GB per buffer)"},
         "roofline": roofline,
         "clocks": clocks,
         "e2e": e2e,

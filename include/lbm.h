@@ -64,9 +64,10 @@ typedef enum {
  * e_x e_y e_z, e_x^2 e_y^2), equilibria and forcing moments of Eqs. 13-14 taken
  * from the D3Q19 rows each vector equals (their mean where several coincide;
  * zero for e_x e_y e_z), rates 1, s_e, s_nu x5, s_q x4, s_pi, and Eq. 15 weights
- * 1/3 (axes), 1/24 (corners).  A D3Q15 context runs the two-pass one-node
- * kernels in every precision; the single-pass variants (lbm_set_tuning), the
- * no-alloc step (lbm_step_static) and batches are D3Q19 only. */
+ * 1/3 (axes), 1/24 (corners).  A D3Q15 context runs the two-pass step (the
+ * two-node kernels for the FP32-arithmetic forms with an even Nx, the one-node
+ * kernels otherwise); the single-pass variants (lbm_set_tuning), the no-alloc
+ * step (lbm_step_static) and batches are D3Q19 only. */
 typedef enum {
   LBM_OP_ORTHOGONAL = 0,
   LBM_OP_NONORTHOGONAL = 1,
