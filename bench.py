@@ -12,11 +12,14 @@ converging density wave into the droplet, which focuses at the centre of an
 R = 40 droplet and makes the run non-finite after about 55 steps (FP64
 included); with W = 3 all forms run the 1000 steps.  The headline line is
 the non-orthogonal operator with FP32 arithmetic and storage; the ``forms``
-object adds both operators in FP64 and FP32 and the FP16-storage form, all on
-the same box.  A "step" is one lattice time step (psi pass + fused pass) over
-the whole box; MLUPS = 1e-6 * nodes * steps / second.
+object adds both operators in FP64 and FP32 and the FP16-storage form, the
+D3Q15 variant of the non-orthogonal operator in the same three precisions, all
+on the same box, and the batched and served forms.  A "step" is one lattice
+time step (psi pass + fused pass) over the whole box; MLUPS = 1e-6 * nodes *
+steps / second.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--forms headline|batched|all]
+                  [--op nonorth|orth|nonorth_d3q15] [--prec f64|f32|f16]
 
 Under torchrun (N > 1) each rank runs its own box on its own GPU (replicas,
 weak scaling); the timed region is bracketed by barriers and the max over
