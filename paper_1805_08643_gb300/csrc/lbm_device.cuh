@@ -109,12 +109,6 @@ template <> struct Storage<__half> {
   }
 };
 
-// Pull the 19 deviations of node x (post-streaming state at time t).
-template <typename S, typename T>
-__device__ __forceinline__ void pull(const S *__restrict__ g, int n, const Nbhd &nb, T f[19]) {
-#pragma unroll
-  for (int a = 0; a < 19; ++a) f[a] = (T)Storage<S>::load(g + (size_t)a * n + nb.src(a), a);
-}
 
 // ------------------------------------------------------------------ EOS
 // psi(rho): square-root form sqrt(2 (p_EOS - rho/3) / G) with the

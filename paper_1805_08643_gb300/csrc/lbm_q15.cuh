@@ -88,12 +88,6 @@ template <> struct Storage<__half> {
   }
 };
 
-template <typename S, typename T>
-__device__ __forceinline__ void pull(const S *__restrict__ g, int n, const Nbhd &nb, T f[kQ]) {
-#pragma unroll
-  for (int a = 0; a < kQ; ++a) f[a] = (T)Storage<S>::load(g + (size_t)a * n + src(nb, a), a);
-}
-
 // rho - rho_ref: the sum of the deviations, in the order of the forward chain.
 template <typename T>
 __device__ __forceinline__ T drho(const T f[kQ]) {
