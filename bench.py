@@ -67,7 +67,7 @@ HEADLINE = ("nonorth", "f32")
 FUSED_DRAM_BYTES = {("nonorth", "f32"): 152.6, ("nonorth", "f16"): 77.4}
 # FP64 instructions per node of the fused pass (ncu instruction counts at 128^3 over the nodes) and the FP64
 # issue peak of one GB300: 2 per SM per clock x 152 SMs x 2070 MHz.
-FUSED_FP64_INSTR = {"nonorth": 255.0, "orth": 309.0}
+FUSED_FP64_INSTR = {"nonorth": 255.0, "orth": 309.0, "nonorth_d3q15": 207.0}
 FP64_PEAK_GINSTR = 2 * 152 * 2070e6 / 1e9
 PREC_TEXT = {"f64": "FP64 compute and storage", "f32": "FP32 compute and storage",
              "f16": "FP32 compute, FP16 storage"}
@@ -587,7 +587,11 @@ def main():
             f_fused = fkt["fused_ms"] / max(fkt["fused_launches"], 1)
             f_psi = fkt["psi_ms"] / max(fkt["psi_launches"], 1)
             fb, pb = FUSED_BYTES_Q15[fprec], PSI_BYTES_Q15[fprec]
-            forms[f"nonorth_d3q15_{fprec}_droplet"] = {
+            extra = {}
+            if fprec == "f64":
+                extra["fp64_alu_frac_fused"] = (FUSED_FP64_INSTR["nonorth_d3q15"] * n / (f_fused / 1e3) / 1e9
+                                                / FP64_PEAK_GINSTR)
+            forms[f"nonorth_d3q15_{fprec}_droplet"] = {**extra,
                 "mlups": n * steps_f / (fms / 1e3) / 1e6, "ms_per_step": fms / steps_f, "fused_ms": f_fused,
                 "psi_ms": f_psi, "fused_gbs": fb * n / (f_fused / 1e3) / 1e9,
                 "hbm_frac_fused": fb * n / (f_fused / 1e3) / 1e9 / hbm_peak,
