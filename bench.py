@@ -596,7 +596,7 @@ def main():
                 "psi_ms": f_psi, "fused_gbs": fb * n / (f_fused / 1e3) / 1e9,
                 "hbm_frac_fused": fb * n / (f_fused / 1e3) / 1e9 / hbm_peak,
                 "step_gbs": (fb + pb) * n / (fms / steps_f / 1e3) / 1e9, "bytes_per_lup_two_pass": fb + pb,
-                "status": fst, "note": "D3Q15 non-orthogonal variant (one-node kernels)"}
+                "status": fst, "note": "D3Q15 non-orthogonal variant (two-node kernels for FP32 arithmetic, one-node for FP64)"}
         for fprec in ("f32", "f16"):
             fms, fkt, _, fst = time_form("nonorth", fprec, args.edge, args.steps, args.warmup, world,
                                          eos_arith="f32x2")
