@@ -5,12 +5,15 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_reference_arm_prints_one_contract_line():
+@pytest.mark.parametrize("op", ["nonorth", "nonorth_d3q15"])
+def test_reference_arm_prints_one_contract_line(op):
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
-                          "--warmup", "3"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+                          "--warmup", "3", "--op", op], capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
@@ -20,4 +23,6 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["config"]["edge"] == 256
+    assert d["config"]["edge"] == 256 and d["config"]["operator"] == op
+    lattice = "D3Q15" if op == "nonorth_d3q15" else "D3Q19"
+    assert d["config"]["workload"].startswith(lattice) and "W=3" in d["config"]["workload"]
