@@ -111,6 +111,19 @@ def test_coinciding_eq9_and_eq10_vectors_on_d3q15():
     assert np.all(M[14] == ex * ex * ez * ez) and np.all(M[14] == ey * ey * ez * ez)
 
 
+def test_rates_are_the_eq11_rates_of_the_coinciding_d3q19_rows():
+    # distinct rates for every group, so a swapped assignment shows
+    p = L.Params(s_e=0.71, s_nu=1.13, s_q=1.27, s_pi=0.93, s_eps=1.5, s_m=1.6)
+    r15, r19 = D.relaxation(p), L.relaxation(p)
+    for k in range(10):
+        assert r15[k] == r19[k]
+    for k, pair in ((10, (10, 15)), (11, (11, 13)), (12, (12, 14))):
+        assert all(r15[k] == r19[k19] for k19 in pair)
+    assert all(r15[14] == r19[k19] for k19 in (16, 17, 18))
+    assert r15[13] == p.s_q  # e_x e_y e_z: third order, the Eq. 11 third-order rate
+    assert L.relaxation(p)[10] == p.s_q and L.relaxation(p)[16] == p.s_pi  # Eq. 11 itself
+
+
 # ---------------------------------------------------------------- equilibria, forcing
 def test_rest_state_is_the_textbook_weights():
     rho = RNG.uniform(0.1, 2.0, 7)
