@@ -117,3 +117,16 @@ def test_d3q15_contexts_size_their_buffers_and_reject_d3q19_only_paths(lbm):
     assert pb.value == 4 * 512 * 8  # 15 halves per node are less than the 4 doubles lbm_moments stages
     lbm.lib.lbm_destroy(h)
     assert _create(lbm, op=3)[0] == lbm.ERR_ARG
+
+
+def test_create_rejects_boxes_beyond_the_index_limits(lbm):
+    # 32-bit node index and 32-bit element offsets (19 N < 2^32), the grid-z launch limit
+    assert _create(lbm, grid=(1024, 1024, 256))[0] == lbm.ERR_ARG  # 19 * 2^28 >= 2^32
+    assert _create(lbm, grid=(2048, 2048, 512))[0] == lbm.ERR_ARG  # N = 2^31
+    assert _create(lbm, grid=(3, 3, 65536))[0] == lbm.ERR_ARG
+    st, h = _create(lbm, grid=(1024, 1024, 200))  # 19 N just under 2^32: accepted (no allocation yet)
+    assert st == lbm.OK
+    lbm.lib.lbm_destroy(h)
+    st, h = _create(lbm, grid=(3, 3, 65535))
+    assert st == lbm.OK
+    lbm.lib.lbm_destroy(h)
