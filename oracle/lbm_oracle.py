@@ -437,15 +437,6 @@ def droplet_density(grid, centre, R, W, rho_l, rho_v) -> np.ndarray:
     return 0.5 * (rho_l + rho_v) - 0.5 * (rho_l - rho_v) * np.tanh(2.0 * (r - R) / W)
 
 
-def droplets_density(grid, centres, radii, W, rho_l, rho_v) -> np.ndarray:
-    """Several droplets: the pointwise maximum of their Eq. 59 profiles."""
-    out = None
-    for c, R in zip(centres, radii):
-        d = droplet_density(grid, c, R, W, rho_l, rho_v)
-        out = d if out is None else np.maximum(out, d)
-    return out
-
-
 def slab_density(grid, axis, lo, hi, W, rho_l, rho_v) -> np.ndarray:
     """Liquid slab between planes lo and hi along one axis (Sec. IV D)."""
     coord = _coords(grid)[axis]
@@ -463,24 +454,3 @@ def total_mass(f: np.ndarray) -> float:
 def total_momentum(p: Params, f: np.ndarray) -> np.ndarray:
     rho, u, _, _ = macroscopic(p, f)
     return (rho * u).reshape(3, -1).sum(axis=1)
-
-
-def laplace_pressure_jump(p: Params, rho: np.ndarray, centre) -> float:
-    """p(rho at the droplet centre) - p(rho at the node farthest from it)."""
-    nx, ny, nz = p.grid
-    c = tuple(int(round(v)) for v in centre)
-    far = ((c[0] + nx // 2) % nx, (c[1] + ny // 2) % ny, (c[2] + nz // 2) % nz)
-    p_in = eos_pressure(rho[c[2], c[1], c[0]], p)
-    p_out = eos_pressure(rho[far[2], far[1], far[0]], p)
-    return float(p_in - p_out)
-
-
-def equimolar_radius(rho: np.ndarray, rho_in: float, rho_out: float) -> float:
-    """R_d of the sphere holding the droplet's liquid volume."""
-    vol = float(((rho - rho_out) / (rho_in - rho_out)).sum())
-    return (3.0 * vol / (4.0 * np.pi)) ** (1.0 / 3.0)
-
-
-def max_speed(u: np.ndarray) -> float:
-    """Maximum spurious velocity magnitude max_x |u(x)|."""
-    return float(np.sqrt((u * u).sum(axis=0)).max())

@@ -233,3 +233,29 @@ def test_variable_viscosity_shear_wave_takes_the_phase_viscosity(op, phase):
     nu = nu_l if phase == "liquid" else nu_v
     assert abs(ratio / np.exp(-nu * k * k * steps) - 1) < 0.003
     assert np.allclose(L.shear_rate_field(p, np.array([2.0, 0.1])), [1 / (3 * nu_l + 0.5), 1 / (3 * nu_v + 0.5)])
+
+
+# ---------------------------------------------------------------- initial fields
+def test_droplet_profile_is_eq59_with_periodic_minimum_image():
+    grid, c, R, W, rl, rv = (20, 16, 12), (10.0, 8.0, 6.0), 4.0, 2.0, 0.3, 0.02
+    rho = L.droplet_density(grid, c, R, W, rl, rv)
+    assert rho.shape == (12, 16, 20)
+    # at the centre tanh(-2R/W); at distance R (node (14, 8, 6)) the mean of the phases
+    assert abs(rho[6, 8, 10] - (0.5 * (rl + rv) + 0.5 * (rl - rv) * np.tanh(4.0))) < 1e-15
+    assert abs(rho[6, 8, 14] - 0.5 * (rl + rv)) < 1e-15
+    # the minimum image: x = 0 lies 10 from the centre either way, x = 19 lies 9 (through the boundary)
+    d9 = 0.5 * (rl + rv) - 0.5 * (rl - rv) * np.tanh(2.0 * (9.0 - R) / W)
+    assert abs(rho[6, 8, 19] - d9) < 1e-15 and abs(rho[6, 8, 1] - d9) < 1e-15
+    # a centre off the grid by one period gives the same field
+    assert np.max(np.abs(L.droplet_density(grid, (30.0, -8.0, 18.0), R, W, rl, rv) - rho)) < 1e-14
+
+
+def test_slab_profile_between_its_planes():
+    grid, lo, hi, W, rl, rv = (3, 2, 64), 16.0, 48.0, 2.0, 0.3, 0.02
+    rho = L.slab_density(grid, 2, lo, hi, W, rl, rv)
+    half = 0.5 * (rl - rv)
+    assert abs(rho[32, 0, 0] - (rv + half * 2 * np.tanh(16.0))) < 1e-15  # mid-slab: liquid
+    assert abs(rho[16, 1, 2] - (rv + half * (0.0 - np.tanh(-32.0)))) < 1e-15  # on the plane lo: the mean
+    assert abs(rho[0, 0, 0] - (rv + half * (np.tanh(-16.0) - np.tanh(-48.0)))) < 1e-15  # vapour
+    assert np.all(rho == rho[:, :1, :1])  # depends on z only
+    assert np.allclose(L.slab_density((64, 2, 3), 0, lo, hi, W, rl, rv)[0, 0, :], rho[:, 0, 0], rtol=0, atol=0)
