@@ -236,11 +236,14 @@ long long lbm_step_count(const lbm_ctx *ctx);
  *    flight at once on one device) race and give wrong results.  Each call
  *    rewrites all psi it reads, so nothing needs clearing between calls.
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ *    first call before any stream capture.  cudaDeviceReset invalidates the
+ *    kept address: do not call this after resetting a device it has run on.
  *  - Asynchronous on the context's stream.  A density outside the EOS domain
  *    gives NaN populations in f_out (there is no error word on this path).
  * Errors: LBM_ERR_ARG (null or aliased pointers, precision, size, a D3Q15 context),
- * LBM_ERR_CUDA. */
+ * LBM_ERR_CUDA (the status of this call's own launches only: an error left
+ * earlier on the calling thread is neither reported nor cleared). */
 lbm_status lbm_step_static(const lbm_ctx *ctx, const double *f_in, double *f_out);
 
 /* ------------------------------------------------------------------ batches
@@ -308,6 +311,11 @@ lbm_status lbm_batch_info(const lbm_batch *b, int *live_boxes, int *work_items, 
 
 /* Steps box id has taken since its initialisation (-1: no such box). */
 long long lbm_batch_box_steps(const lbm_batch *b, int id);
+
+/* How many times the batch has uploaded its descriptor and work-item tables and
+ * captured its step graphs (after boxes join, leave, are initialised or retuned;
+ * stepping alone, odd or even counts, never rebuilds).  -1 for a NULL batch. */
+long long lbm_batch_graph_builds(const lbm_batch *b);
 
 const char *lbm_batch_last_error(const lbm_batch *b);
 void lbm_batch_destroy(lbm_batch *b);

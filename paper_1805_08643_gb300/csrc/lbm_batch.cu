@@ -59,7 +59,12 @@ struct lbm_batch {
   int cap_red = 0;
   bool dirty = true;         // descriptors / items need uploading, graphs re-capturing
   bool pair = false;         // the captured step is the two-pass pair kernels
-  cudaGraphExec_t g2 = nullptr, g1 = nullptr;
+  // graphs of two steps and of one step, for each starting parity: the state of
+  // box h is at level h.d.cur ^ phase, and a step at parity `phase` moves it to
+  // the other level, so an odd step count flips phase instead of the descriptors
+  cudaGraphExec_t g2[2] = {nullptr, nullptr}, g1[2] = {nullptr, nullptr};
+  int phase = 0;
+  long long builds = 0;      // descriptor uploads and graph captures so far
   long long steps = 0;
   std::string err;
 };
@@ -89,13 +94,19 @@ size_t box_bytes(int precision, long long n) {
 int default_zc(const KParams &P) { return std::min(P.nz, 32); }
 
 void destroy_graphs(lbm_batch *b) {
-  if (b->g2) cudaGraphExecDestroy(b->g2);
-  if (b->g1) cudaGraphExecDestroy(b->g1);
-  b->g2 = b->g1 = nullptr;
+  for (int p = 0; p < 2; ++p) {
+    if (b->g2[p]) cudaGraphExecDestroy(b->g2[p]);
+    if (b->g1[p]) cudaGraphExecDestroy(b->g1[p]);
+    b->g2[p] = b->g1[p] = nullptr;
+  }
 }
 
 // Upload descriptors and the work-item table (largest boxes first), recapture graphs.
 lbm_status rebuild(lbm_batch *b) {
+  // fold the phase into the descriptors: afterwards level d.cur holds each state
+  for (auto &h : b->boxes)
+    if (h.live) h.d.cur ^= b->phase;
+  b->phase = 0;
   const int nb = (int)b->boxes.size();
   if (nb > b->cap_boxes) {
     if (b->d_boxes) cudaFreeAsync(b->d_boxes, b->stream);
@@ -147,11 +158,12 @@ lbm_status rebuild(lbm_batch *b) {
                   : lbm::launch_batch_onepass(b->precision, b->eos, b->tile, b->d_boxes, b->d_items, b->nitems,
                                               parity, grid, b->d_err, b->stream);
     };
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < 4; ++k) {  // g2[0], g2[1], g1[0], g1[1]
+      const int two = k < 2, p0 = k & 1;
       cudaGraph_t g;
       BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-      cudaError_t e = step(0);
-      if (e == cudaSuccess && k == 0) e = step(1);
+      cudaError_t e = step(p0);
+      if (e == cudaSuccess && two) e = step(p0 ^ 1);
       cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
       if (e != cudaSuccess || e2 != cudaSuccess) {
         if (e2 == cudaSuccess) cudaGraphDestroy(g);
@@ -161,9 +173,10 @@ lbm_status rebuild(lbm_batch *b) {
       e = cudaGraphInstantiate(&x, g, 0);
       cudaGraphDestroy(g);
       BCK(e, "graph instantiate");
-      (k == 0 ? b->g2 : b->g1) = x;
+      (two ? b->g2 : b->g1)[p0] = x;
     }
   }
+  ++b->builds;
   b->dirty = false;
   return LBM_OK;
 }
@@ -181,13 +194,16 @@ lbm::Launch launch_of(lbm_batch *b) {
   return L;
 }
 
-void *cur_g(HostBox *h) { return h->d.g[h->d.cur]; }
-float *cur_psi(HostBox *h) { return h->d.psi[h->d.cur]; }
+// Level of a box's current state (see lbm_batch::phase).
+int cur_level(const lbm_batch *b, const HostBox *h) { return h->d.cur ^ b->phase; }
+void *cur_g(const lbm_batch *b, HostBox *h) { return h->d.g[cur_level(b, h)]; }
+float *cur_psi(const lbm_batch *b, HostBox *h) { return h->d.psi[cur_level(b, h)]; }
+void *spare_g(const lbm_batch *b, HostBox *h) { return h->d.g[cur_level(b, h) ^ 1]; }
 
 lbm_status finish_box_init(lbm_batch *b, HostBox *h, const double *rho_dev) {
   const lbm::Launch L = launch_of(b);
-  BCK(lbm::launch_state_from_rho(h->d.P, h->precision, rho_dev, cur_g(h), L), "state_from_rho");
-  BCK(lbm::launch_psi(h->d.P, h->precision, cur_g(h), cur_psi(h), b->d_err, L), "psi");
+  BCK(lbm::launch_state_from_rho(h->d.P, h->precision, rho_dev, cur_g(b, h), L), "state_from_rho");
+  BCK(lbm::launch_psi(h->d.P, h->precision, cur_g(b, h), cur_psi(b, h), b->d_err, L), "psi");
   BCK(cudaMemsetAsync(h->u_prev, 0, sizeof(float) * 3 * (size_t)h->d.P.n, b->stream), "clear u_prev");
   h->initialised = true;
   h->steps = 0;
@@ -264,7 +280,7 @@ lbm_status lbm_batch_add(lbm_batch *b, const int grid[3], const lbm_eos *eos, do
   h.d.psi[1] = (float *)(m + 2 * pop + ps);
   h.u_prev = (float *)(m + 2 * pop + 2 * ps);
   h.d.op = op;
-  h.d.cur = 0;
+  h.d.cur = b->phase;  // its state starts at level 0
   b->used += bytes;
   int slot = -1;
   for (int i = 0; i < (int)b->boxes.size(); ++i)
@@ -305,7 +321,7 @@ lbm_status lbm_batch_init_droplet(lbm_batch *b, int id, const double centre[3], 
   ch.cy[0] = centre[1];
   ch.cz[0] = centre[2];
   ch.r[0] = R;
-  double *rho = (double *)h->d.g[h->d.cur ^ 1];
+  double *rho = (double *)spare_g(b, h);
   BCK(lbm::launch_rho_droplets(h->d.P, rho, ch, W, rho_l, rho_v, true, launch_of(b)), "rho_droplets");
   return finish_box_init(b, h, rho);
 }
@@ -317,7 +333,7 @@ lbm_status lbm_batch_init_flat(lbm_batch *b, int id, int axis, double lo, double
     return bfail(b, LBM_ERR_ARG, "bad slab");
   h->d.P.rho_ref = rho_v;
   lbm::refresh_float_params(h->d.P);
-  double *rho = (double *)h->d.g[h->d.cur ^ 1];
+  double *rho = (double *)spare_g(b, h);
   BCK(lbm::launch_rho_slab(h->d.P, rho, axis, lo, hi, W, rho_l, rho_v, launch_of(b)), "rho_slab");
   return finish_box_init(b, h, rho);
 }
@@ -341,12 +357,10 @@ lbm_status lbm_batch_step(lbm_batch *b, int n) {
     if (s != LBM_OK) return s;
   }
   if (!b->nitems) return LBM_OK;
-  for (int k = 0; k + 1 < n; k += 2) BCK(cudaGraphLaunch(b->g2, b->stream), "graph launch");
+  for (int k = 0; k + 1 < n; k += 2) BCK(cudaGraphLaunch(b->g2[b->phase], b->stream), "graph launch");
   if (n & 1) {
-    BCK(cudaGraphLaunch(b->g1, b->stream), "graph launch");
-    for (auto &h : b->boxes)
-      if (h.live && h.initialised) h.d.cur ^= 1;
-    b->dirty = true;  // descriptors changed: parity 0 now means the other level
+    BCK(cudaGraphLaunch(b->g1[b->phase], b->stream), "graph launch");
+    b->phase ^= 1;  // every box's state is now at the other level
   }
   for (auto &h : b->boxes)
     if (h.live && h.initialised) h.steps += n;
@@ -360,11 +374,11 @@ lbm_status lbm_batch_moments(lbm_batch *b, int id, double *rho, double *u, int o
   const lbm::Launch L = launch_of(b);
   const size_t n = h->d.P.n;
   if (on_device) {
-    BCK(lbm::launch_moments(h->d.P, h->precision, cur_g(h), cur_psi(h), rho, u, L), "moments");
+    BCK(lbm::launch_moments(h->d.P, h->precision, cur_g(b, h), cur_psi(b, h), rho, u, L), "moments");
     return LBM_OK;
   }
-  double *tmp = (double *)h->d.g[h->d.cur ^ 1];  // 4N doubles fit in a population buffer
-  BCK(lbm::launch_moments(h->d.P, h->precision, cur_g(h), cur_psi(h), tmp, tmp + n, L), "moments");
+  double *tmp = (double *)spare_g(b, h);  // 4N doubles fit in a population buffer
+  BCK(lbm::launch_moments(h->d.P, h->precision, cur_g(b, h), cur_psi(b, h), tmp, tmp + n, L), "moments");
   if (rho) BCK(cudaMemcpyAsync(rho, tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, b->stream), "D2H rho");
   if (u) BCK(cudaMemcpyAsync(u, tmp + n, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, b->stream), "D2H u");
   BCK(cudaStreamSynchronize(b->stream), "sync");
@@ -376,7 +390,7 @@ lbm_status lbm_batch_diag(lbm_batch *b, int id, double out[5]) {
   if (!h || !h->initialised || !out) return bfail(b, LBM_ERR_ARG, "bad box or output");
   double *part = (double *)((char *)b->d_scratch + lbm::kScratchPartialOffset);
   double *res = (double *)((char *)b->d_scratch + lbm::kScratchResultOffset);
-  BCK(lbm::launch_diag(h->d.P, h->precision, cur_g(h), cur_psi(h), part, res, launch_of(b)), "diag");
+  BCK(lbm::launch_diag(h->d.P, h->precision, cur_g(b, h), cur_psi(b, h), part, res, launch_of(b)), "diag");
   BCK(cudaMemcpyAsync(out, res, 5 * sizeof(double), cudaMemcpyDeviceToHost, b->stream), "D2H diag");
   BCK(cudaStreamSynchronize(b->stream), "sync");
   return LBM_OK;
@@ -394,7 +408,7 @@ lbm_status lbm_batch_max_du(lbm_batch *b, int nid, const int *ids, double *out) 
   for (int k = 0; k < nid; ++k) {
     HostBox *h = get_box(b, ids[k]);
     if (!h || !h->initialised) return bfail(b, LBM_ERR_ARG, "bad box id");
-    BCK(lbm::launch_max_du(h->d.P, h->precision, cur_g(h), cur_psi(h), h->u_prev, b->d_red + k, launch_of(b)),
+    BCK(lbm::launch_max_du(h->d.P, h->precision, cur_g(b, h), cur_psi(b, h), h->u_prev, b->d_red + k, launch_of(b)),
         "max_du");
   }
   BCK(cudaMemcpyAsync(out, b->d_red, sizeof(double) * nid, cudaMemcpyDeviceToHost, b->stream), "D2H");
@@ -422,6 +436,8 @@ lbm_status lbm_batch_info(const lbm_batch *b, int *live_boxes, int *work_items, 
   if (bytes_used) *bytes_used = b->used;
   return LBM_OK;
 }
+
+long long lbm_batch_graph_builds(const lbm_batch *b) { return b ? b->builds : -1; }
 
 long long lbm_batch_box_steps(const lbm_batch *b, int id) {
   if (!b || id < 0 || id >= (int)b->boxes.size() || !b->boxes[id].live) return -1;

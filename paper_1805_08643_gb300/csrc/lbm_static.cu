@@ -67,7 +67,11 @@ __global__ void static_fused_kernel(const double *__restrict__ f_in, double *__r
   for (int a = 0; a < 19; ++a) f_out[(size_t)a * P.n + nb.dst(a)] = f[a];
 }
 
-// Device address of lbm_static_psi, looked up once per device.
+// Device address of lbm_static_psi, looked up on the first call on each device
+// (with that device current) and kept for the life of the process.  A
+// cudaDeviceReset frees the module that holds the array, so the kept address
+// is stale after one: this entry point is not for processes that reset a
+// device they have called it on.
 constexpr int kMaxDevices = 64;
 double *g_psi_addr[kMaxDevices] = {nullptr};
 
@@ -86,6 +90,14 @@ cudaError_t static_psi_address(double **out) {
   return cudaSuccess;
 }
 
+// Launch through cudaLaunchKernel, whose return value is this launch's own
+// status: an unrelated error left earlier on the calling thread is neither
+// reported as this step's failure nor cleared.
+template <typename K>
+cudaError_t launch(K kernel, dim3 grid, dim3 block, cudaStream_t stream, void **args) {
+  return cudaLaunchKernel((const void *)kernel, grid, block, args, 0, stream);
+}
+
 }  // namespace
 
 extern "C" lbm_status lbm_step_static(const lbm_ctx *ctx, const double *f_in, double *f_out) {
@@ -102,17 +114,21 @@ extern "C" lbm_status lbm_step_static(const lbm_ctx *ctx, const double *f_in, do
   double *psi = nullptr;
   if (static_psi_address(&psi) != cudaSuccess) return LBM_ERR_CUDA;
   const dim3 block(32, 4), grid((P.nx + 31) / 32, (P.ny + 3) / 4, P.nz);
+  void *psi_args[] = {(void *)&f_in, (void *)&psi, (void *)&P};
+  cudaError_t e;
   switch (P.eos) {
-    case lbm::kEosCS: static_psi_kernel<lbm::kEosCS><<<grid, block, 0, stream>>>(f_in, psi, P); break;
-    case lbm::kEosExp: static_psi_kernel<lbm::kEosExp><<<grid, block, 0, stream>>>(f_in, psi, P); break;
-    default: static_psi_kernel<lbm::kEosNone><<<grid, block, 0, stream>>>(f_in, psi, P); break;
+    case lbm::kEosCS: e = launch(static_psi_kernel<lbm::kEosCS>, grid, block, stream, psi_args); break;
+    case lbm::kEosExp: e = launch(static_psi_kernel<lbm::kEosExp>, grid, block, stream, psi_args); break;
+    default: e = launch(static_psi_kernel<lbm::kEosNone>, grid, block, stream, psi_args); break;
   }
-  if (op == lbm::kNonOrth) {
-    if (sigma_on) static_fused_kernel<lbm::kNonOrth, true><<<grid, block, 0, stream>>>(f_in, f_out, psi, P);
-    else static_fused_kernel<lbm::kNonOrth, false><<<grid, block, 0, stream>>>(f_in, f_out, psi, P);
-  } else {
-    if (sigma_on) static_fused_kernel<lbm::kOrth, true><<<grid, block, 0, stream>>>(f_in, f_out, psi, P);
-    else static_fused_kernel<lbm::kOrth, false><<<grid, block, 0, stream>>>(f_in, f_out, psi, P);
-  }
-  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+  if (e != cudaSuccess) return LBM_ERR_CUDA;
+  const double *psi_c = psi;
+  void *fused_args[] = {(void *)&f_in, (void *)&f_out, (void *)&psi_c, (void *)&P};
+  if (op == lbm::kNonOrth)
+    e = sigma_on ? launch(static_fused_kernel<lbm::kNonOrth, true>, grid, block, stream, fused_args)
+                 : launch(static_fused_kernel<lbm::kNonOrth, false>, grid, block, stream, fused_args);
+  else
+    e = sigma_on ? launch(static_fused_kernel<lbm::kOrth, true>, grid, block, stream, fused_args)
+                 : launch(static_fused_kernel<lbm::kOrth, false>, grid, block, stream, fused_args);
+  return e == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

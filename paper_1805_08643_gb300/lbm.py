@@ -79,6 +79,7 @@ SIGNATURES = {
     "lbm_batch_check": (_c_int, [_vp]),
     "lbm_batch_info": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), _szp]),
     "lbm_batch_box_steps": (ctypes.c_longlong, [_vp, _c_int]),
+    "lbm_batch_graph_builds": (ctypes.c_longlong, [_vp]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_vp]),
     "lbm_batch_destroy": (None, [_vp]),
     "lbm_destroy": (None, [_vp]),
@@ -393,7 +394,8 @@ class Batch:
     def info(self):
         lb, wi, by = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
         self._check(lib.lbm_batch_info(self._h, ctypes.byref(lb), ctypes.byref(wi), ctypes.byref(by)), "lbm_batch_info")
-        return {"live_boxes": lb.value, "work_items": wi.value, "bytes_used": by.value}
+        return {"live_boxes": lb.value, "work_items": wi.value, "bytes_used": by.value,
+                "graph_builds": lib.lbm_batch_graph_builds(self._h)}
 
     def box_steps(self, box):
         return lib.lbm_batch_box_steps(self._h, box)

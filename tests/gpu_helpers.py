@@ -8,11 +8,18 @@ from oracle import maxwell
 A, B, R_GAS = 1.0, 4.0, 1.0
 
 
-def physics(T_over_Tc=0.8, s_nu=1.0, other=1.1, G=-1.0, sigma=0.0, eos="cs"):
-    """Carnahan-Starling droplet physics of the 32^3 parity workload."""
+def physics(T_over_Tc=0.8, s_nu=1.0, other=1.1, G=-1.0, sigma=0.0, eos="cs", rates=None):
+    """Carnahan-Starling droplet physics of the 32^3 parity workload.
+
+    rates: a dict of relaxation rates (s_e, s_nu, s_q, s_pi, s_eps, s_m) that replaces
+    the s_nu / other pair, e.g. six distinct rates.
+    """
     Tc = L.critical_temperature(A, B, R_GAS)
-    return dict(eos=eos, a=A, b=B, R=R_GAS, T=T_over_Tc * Tc, G=G, sigma=sigma,
-                s_e=other, s_nu=s_nu, s_q=other, s_pi=other, s_eps=other, s_m=other)
+    d = dict(eos=eos, a=A, b=B, R=R_GAS, T=T_over_Tc * Tc, G=G, sigma=sigma,
+             s_e=other, s_nu=s_nu, s_q=other, s_pi=other, s_eps=other, s_m=other)
+    if rates:
+        d.update(rates)
+    return d
 
 
 def oracle_params(grid, op, phys):

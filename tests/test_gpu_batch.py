@@ -167,3 +167,25 @@ def test_max_du_tracks_convergence():
     d2 = b.max_du([box])[0]
     assert d1 > 0 and d2 > 0 and d2 < d1  # a static droplet relaxes
     b.close()
+
+
+def test_odd_step_counts_neither_rebuild_nor_change_the_result():
+    """1 + 1 steps equal 2 steps bit for bit, and stepping one at a time recaptures nothing
+    (the batch keeps a graph per starting parity)."""
+    results = []
+    for chunks in ([2], [1, 1], [1, 2, 1, 1, 3]):
+        b = _batch()
+        ids = [_add(b, s) for s in BOXES[:2]]
+        b.step(chunks[0])
+        builds = b.info()["graph_builds"]
+        for n in chunks[1:]:
+            b.step(n)
+        assert b.info()["graph_builds"] == builds, chunks
+        total = sum(chunks)
+        assert all(b.box_steps(i) == total for i in ids)
+        results.append((total, [b.moments(i) for i in ids]))
+        b.close()
+    (t0, r0), (t1, r1), _ = results
+    assert t0 == t1 == 2
+    for (a_rho, a_u), (b_rho, b_u) in zip(r0, r1):
+        assert np.array_equal(a_rho, b_rho) and np.array_equal(a_u, b_u)
