@@ -193,14 +193,34 @@ lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
  * pass of the next step trails the fused pass by one plane, reading the new
  * populations from L2; results equal the two-pass step bit for bit; the first
  * call in this mode allocates a small device array of progress flags (one int
- * per 64x4 tile and plane), freed by lbm_destroy.  tile picks the x-y tile of
+ * per 64x4 tile and plane), freed by lbm_destroy.  5 (same forms, D3Q19)
+ * runs each step as one cooperative launch over an ordered work list: each
+ * item is the fused pass of one 64x4 tile of one plane plus the psi pass of
+ * the next step for another tile, placed (and checked, on the host) at least
+ * one wave of the grid after the 27 fused tiles it reads; the FP64 EOS of the
+ * psi work overlaps the fused work's HBM stream and the populations it pulls
+ * come from L2 (Eqs. 3-6 in 2 x 19 x s + 8 bytes per node); results equal the
+ * two-pass step bit for bit; the first step in this mode allocates the item
+ * table and counters (about 20 bytes per tile and plane), freed by
+ * lbm_destroy.  tile picks the x-y tile of
  * the single-pass kernel (0: 32x4, 1: 32x8, 2: 64x4); z_planes the z planes
  * each thread block marches through (0 = automatic).  Results do not depend on
  * tile or z_planes.  Errors: LBM_ERR_ARG (bad value, a mode the context's
  * precision or Nx does not support, or a single-pass mode on a D3Q15 context);
- * LBM_ERR_OOM / LBM_ERR_CUDA (mode 4's flag
- * array could not be allocated). */
+ * LBM_ERR_OOM / LBM_ERR_CUDA (mode 4's flag array or mode 5's item table
+ * could not be allocated, at the first step in mode 5). */
 lbm_status lbm_set_tuning(lbm_ctx *ctx, int single_pass, int tile, int z_planes);
+
+/* Budget of the bounded device-side waits of the single-pass kernels (modes 2-5):
+ * a wait polls at most spin_limit times (a few tens of nanoseconds apart) and
+ * then gives up: it sets the context's error word (lbm_check returns
+ * LBM_ERR_TIMEOUT) and the kernel goes on to its end, so no launch can hang.
+ * spin_limit <= 0 restores the default, 2^22.  inject_unreachable != 0 is a
+ * host-side fault injection for tests: every cross-block wait of modes 4 and 5
+ * then waits for a count no block reaches, so each such wait runs out its
+ * budget (the results of those steps are not meaningful; set it back to 0 and
+ * re-initialise).  Takes effect at the next lbm_step.  Errors: LBM_ERR_ARG. */
+lbm_status lbm_set_wait_budget(lbm_ctx *ctx, int spin_limit, int inject_unreachable);
 
 /* Density-dependent shear viscosity (Sec. IV D: raising nu_V / nu_L lowers the
  * spurious currents; the paper gives no rule).  nu(rho) is linear in rho from

@@ -37,6 +37,10 @@ struct lbm_ctx {
   int *flags = nullptr;     // its per-(tile, plane) progress flags
   size_t nflags = 0;
   int stamp = 0;
+  bool queued = false;      // single pass on the ordered work queue (FP32 arithmetic, D3Q19, Nx even)
+  lbm::QueueState q{};      // its item table and counters (one allocation: q_mem)
+  void *q_mem = nullptr;
+  int q_stamp = 0;
   bool eos_f2 = false;      // EOS radicand in compensated FP32 pairs (psi pass)
   int tile = 1, zc = 0;     // its tile shape and z planes per CTA (0 = automatic)
   bool owns = false, have_buffers = false, initialized = false, psi_valid = false;
@@ -139,6 +143,37 @@ cudaError_t timed(lbm_ctx *c, int kind, F &&launch) {
   cudaEventRecord(b, c->L.stream);
   c->recs.push_back({a, b, kind});
   return e;
+}
+
+void free_queue(lbm_ctx *c) {
+  if (c->q_mem) cudaFree(c->q_mem);
+  c->q_mem = nullptr;
+  c->q = lbm::QueueState{};
+  c->q_stamp = 0;
+}
+
+// Item table and counters of the work-list single pass (zeroed counters).
+lbm_status ensure_queue(lbm_ctx *c) {
+  if (c->q_mem) return LBM_OK;
+  int grid = 0;
+  CK(lbm::queue_grid(c->precision, &grid), "work list occupancy");
+  std::vector<int4> items;
+  if (!lbm::queue_items(c->P, grid, items)) return fail(c, LBM_ERR_ARG, "no valid work list for this box");
+  const size_t ib = (items.size() * sizeof(int4) + 255) / 256 * 256;
+  const size_t db = lbm::queue_counters(c->P) * sizeof(int);
+  void *m = nullptr;
+  CK(cudaMalloc(&m, ib + db), "cudaMalloc(work list)");
+  c->q_mem = m;
+  c->q.items = (const int4 *)m;
+  c->q.nitems = (int)items.size();
+  c->q.grid = grid;
+  c->q.done = (int *)((char *)m + ib);
+  c->q_stamp = 0;
+  CK(cudaMemcpyAsync(m, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, c->L.stream),
+     "H2D work list");
+  CK(cudaMemsetAsync((char *)m + ib, 0, db, c->L.stream), "clear work list counters");
+  CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");  // the host table goes out of scope
+  return LBM_OK;
 }
 
 lbm_status refresh_psi(lbm_ctx *c) {
@@ -306,10 +341,14 @@ lbm_status lbm_step(lbm_ctx *c, int n) {
   if (!c) return LBM_ERR_ARG;
   if (n < 1) return fail(c, LBM_ERR_ARG, "n must be >= 1");
   if (!c->initialized) return fail(c, LBM_ERR_STATE, "lbm_step before an init");
-  if ((c->onepass || c->lagged) && !c->psi_valid) {
+  if (c->queued) {
+    lbm_status s = ensure_queue(c);
+    if (s != LBM_OK) return s;
+  }
+  if ((c->onepass || c->lagged || c->queued) && !c->psi_valid) {
     CK(timed(c, 0, [&] {
          return lbm::launch_psi(c->P, c->precision, c->g[c->cur], cur_psi(c), err_word(c), c->L,
-                                c->lagged && c->eos_f2);
+                                (c->lagged || c->queued) && c->eos_f2);
        }),
        "psi kernel");
     c->psi_valid = true;
@@ -317,7 +356,18 @@ lbm_status lbm_step(lbm_ctx *c, int n) {
   const int zc = c->zc > 0 ? c->zc : auto_zc(c);
   for (int k = 0; k < n; ++k) {
     void *gin = c->g[c->cur], *gout = c->g[c->cur ^ 1];
-    if (c->lagged) {
+    if (c->queued) {
+      void *pin = cur_psi(c), *pout = psi_at(c, c->pc ^ 1);
+      const int stamp = ++c->q_stamp;
+      CK(timed(c, 1, [&] {
+           return lbm::launch_queue(c->P, c->precision, c->op, c->sigma_on, c->eos_f2, gin, gout, pin, pout, c->q,
+                                    stamp, err_word(c), c->L.stream);
+         }),
+         "single-pass kernel");
+      c->pc ^= 1;
+      c->cur ^= 1;
+      c->psi_valid = true;
+    } else if (c->lagged) {
       void *pin = cur_psi(c), *pout = psi_at(c, c->pc ^ 1);
       const int stamp = ++c->stamp;
       CK(timed(c, 1, [&] {
@@ -468,7 +518,7 @@ lbm_status lbm_kernel_times(lbm_ctx *c, double *ms_psi, long long *n_psi, double
 }
 
 lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
-  if (!c || single_pass < 0 || single_pass > 4 || tile < 0 || tile > 2 || z_planes < 0)
+  if (!c || single_pass < 0 || single_pass > 5 || tile < 0 || tile > 2 || z_planes < 0)
     return fail(c, LBM_ERR_ARG, "bad tuning");
   if (single_pass && c->precision == LBM_F64) return fail(c, LBM_ERR_ARG, "single pass needs FP32 arithmetic");
   if (single_pass && c->P.q == 15) return fail(c, LBM_ERR_ARG, "the single-pass variants are D3Q19 kernels");
@@ -476,6 +526,8 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
     return fail(c, LBM_ERR_ARG, "bulk-copy single pass needs FP32 storage, Nx % 4 == 0 and Nx >= 40");
   if (single_pass == 3 && !lbm::onchip_supported(c->P, c->precision))
     return fail(c, LBM_ERR_ARG, "on-chip-psi single pass needs FP32 arithmetic and an even Nx");
+  if (single_pass == 5 && !lbm::queue_supported(c->P, c->precision))
+    return fail(c, LBM_ERR_ARG, "work-queue single pass needs FP32 arithmetic and an even Nx");
   if (single_pass == 4) {
     if (!lbm::lagged_supported(c->P, c->precision))
       return fail(c, LBM_ERR_ARG, "trailing-psi single pass needs FP32 arithmetic and an even Nx");
@@ -491,6 +543,7 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
     }
   }
   c->psi_valid = false;
+  c->queued = single_pass == 5;
   c->lagged = single_pass == 4;
   c->onchip = single_pass == 3;
   c->onepass = single_pass == 1 || single_pass == 2;
@@ -527,9 +580,17 @@ lbm_status lbm_set_eos_arith(lbm_ctx *c, int mode) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_wait_budget(lbm_ctx *c, int spin_limit, int inject_unreachable) {
+  if (!c) return LBM_ERR_ARG;
+  c->P.spin_limit = spin_limit > 0 ? spin_limit : lbm::kDefaultSpinLimit;
+  c->P.wait_bias = inject_unreachable ? 1 : 0;
+  return LBM_OK;
+}
+
 lbm_status lbm_get_tuning(const lbm_ctx *c, int *single_pass, int *tile, int *z_planes) {
   if (!c) return LBM_ERR_ARG;
-  if (single_pass) *single_pass = c->lagged ? 4 : c->onchip ? 3 : c->onepass ? (c->onepass_tma ? 2 : 1) : 0;
+  if (single_pass)
+    *single_pass = c->queued ? 5 : c->lagged ? 4 : c->onchip ? 3 : c->onepass ? (c->onepass_tma ? 2 : 1) : 0;
   if (tile) *tile = c->tile;
   if (z_planes) *z_planes = c->zc > 0 ? c->zc : auto_zc(c);
   return LBM_OK;
@@ -539,9 +600,10 @@ long long lbm_step_count(const lbm_ctx *c) { return c ? c->steps : -1; }
 
 void lbm_destroy(lbm_ctx *c) {
   if (!c) return;
-  if (c->have_buffers || !c->pool.empty() || c->flags) cudaStreamSynchronize(c->L.stream);
+  if (c->have_buffers || !c->pool.empty() || c->flags || c->q_mem) cudaStreamSynchronize(c->L.stream);
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   if (c->flags) cudaFree(c->flags);
+  free_queue(c);
   if (c->owns) {
     cudaFree(c->g[0]);
     cudaFree(c->g[1]);
@@ -624,6 +686,8 @@ bool fill_params(const int grid[3], const lbm_eos *eos, double G, const lbm_rate
     P.q4 = k * (aa * cc * cc * cc);
     P.f_rho_max = eos->b > 0 ? (float)(4.0 / eos->b) : 0.0f;
   }
+  P.spin_limit = kDefaultSpinLimit;
+  P.wait_bias = 0;
   refresh_float_params(P);
   *out = P;
   return true;

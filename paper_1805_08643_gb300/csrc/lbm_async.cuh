@@ -25,10 +25,11 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, u
                : "memory");
 }
 
-// Wait (acquire) for the phase with the given parity to complete; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+// Wait (acquire) for the phase with the given parity to complete; false if it
+// gave up after `limit` polls (KParams::spin_limit).
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, int limit) {
   const unsigned a = smem_addr(bar);
-  for (int it = 0; it < (1 << 22); ++it) {
+  for (int it = 0; it < limit; ++it) {
     unsigned done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"

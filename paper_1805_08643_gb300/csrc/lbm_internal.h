@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace lbm {
 
 enum Precision { kF64 = 0, kF32 = 1, kF16 = 2 };
@@ -48,7 +50,14 @@ struct KParams {
   float qh[5], ql[5], rr_h, rr_l;
   // the same radicand as a quintic in d = rho - rho_ref: sum_k c[k] d^k
   double c[6];
+  // bounded device-side waits (single-pass kernels): polls before a wait gives
+  // up and sets kErrTimeout; wait_bias is added to every cross-block wait
+  // target (0; 1 makes the targets unreachable, a host-side fault injection)
+  int spin_limit;
+  int wait_bias;
 };
+
+constexpr int kDefaultSpinLimit = 1 << 22;
 
 // Layout of the scratch buffer.
 constexpr int kReduceBlocks = 1024;
@@ -172,6 +181,27 @@ bool lagged_supported(const KParams &P, int precision);
 size_t lagged_flag_count(const KParams &P);
 cudaError_t launch_lagged(const KParams &P, int precision, int op, bool sigma, bool df, const void *g_in, void *g_out,
                           const void *psi_in, void *psi_out, int *flags, int stamp, unsigned *err, cudaStream_t s);
+
+// Single-pass step on an ordered work list (FP32 arithmetic, D3Q19, Nx even):
+// items of a fused tile job and a lagging psi tile job, one cooperative launch
+// of `grid` blocks (queue_grid) working through the list queue_items builds
+// (and checks: false if it cannot).  The device side: the item table and a
+// completion counter per fused job (queue_counters ints, zero before the
+// first launch).
+struct QueueState {
+  const int4 *items;
+  int nitems;
+  int grid;
+  int *done;
+};
+bool queue_supported(const KParams &P, int precision);
+cudaError_t queue_grid(int precision, int *grid);
+size_t queue_counters(const KParams &P);
+bool queue_items(const KParams &P, int grid, std::vector<int4> &out);
+// stamp: 1 + the number of earlier launches on these counters.
+cudaError_t launch_queue(const KParams &P, int precision, int op, bool sigma, bool df, const void *g_in, void *g_out,
+                         const void *psi_in, void *psi_out, const QueueState &q, int stamp, unsigned *err,
+                         cudaStream_t s);
 
 size_t storage_bytes(int precision);  // bytes per stored population
 size_t psi_elem_bytes(int precision);

@@ -54,17 +54,20 @@ __device__ __forceinline__ void store_flag(int *f, int v) {
 }
 
 // Wait until the tiles around tile t (and t) have published plane z of launch
-// `stamp`: thread k < 9 watches neighbour k; then the block synchronises.
-__device__ __forceinline__ bool wait_neighbours(const int *flags, const Tiles &T, int t, int z, int nz, int stamp) {
+// `stamp` (plus P.wait_bias): thread k < 9 watches neighbour k, at most
+// P.spin_limit polls; then the block synchronises.
+__device__ __forceinline__ bool wait_neighbours(const int *flags, const Tiles &T, int t, int z, int nz, int stamp,
+                                                const KParams &P) {
   bool ok = true;
   const int k = threadIdx.y * TXP + threadIdx.x;
   if (k < 9) {
     const int tx = t % T.nx_t, ty = t / T.nx_t;
     const int nxt = (tx + (k % 3) - 1 + T.nx_t) % T.nx_t, nyt = (ty + (k / 3) - 1 + T.ny_t) % T.ny_t;
     const int *f = flags + (size_t)(nyt * T.nx_t + nxt) * nz + z;
+    const int target = stamp + P.wait_bias;
     int it = 0;
-    while (load_flag(f) < stamp) {
-      if (++it > (1 << 22)) {
+    while (load_flag(f) < target) {
+      if (++it > P.spin_limit) {
         ok = false;
         break;
       }
@@ -80,74 +83,15 @@ __device__ __forceinline__ void fused_plane(const S *__restrict__ g_in, S *__res
                                             int z, const Rates<V2> &r) {
   const int x = (t % T.nx_t) * 2 * TXP + 2 * threadIdx.x, y = (t / T.nx_t) * TYR + threadIdx.y;
   if (x >= P.nx || y >= P.ny) return;
-  const PairX px{x, x == 0 ? P.nx - 1 : x - 1, x + 2 >= P.nx ? x + 2 - P.nx : x + 2};
-  const Nbhd nb(x, y, z, P);
-  // the force first, from psi, then the populations: the two sets of 19 pairs
-  // are never live together, which keeps the registers (and so more blocks
-  // resident) down
-  V2 Fx, Fy, Fz, dS4;
-  {
-  V2 p[19];
-  auto row3 = [&](int row, V2 &c, V2 &plus, V2 &minus) {
-    const float2 m = __ldg((const float2 *)(psi + row + px.x));
-    const float l = __ldg(psi + row + px.xm1), rr = __ldg(psi + row + px.xp2);
-    c = V2(m);
-    plus = V2(m.y, rr);
-    minus = V2(l, m.x);
-  };
-  auto row1 = [&](int row) { return V2(__ldg((const float2 *)(psi + row + px.x))); };
-  row3(nb.r00, p[0], p[1], p[2]);
-  row3(nb.rp0, p[3], p[7], p[10]);
-  row3(nb.rm0, p[4], p[9], p[8]);
-  row3(nb.r0p, p[5], p[11], p[14]);
-  row3(nb.r0m, p[6], p[13], p[12]);
-  p[15] = row1(nb.rpp);
-  p[16] = row1(nb.rmm);
-  p[17] = row1(nb.rpm);
-  p[18] = row1(nb.rmp);
-  force_pair<SIGMA>(p, P, Fx, Fy, Fz, dS4);
-  }
-  V2 f[19];
-  pull_pair<S>(g_in, (unsigned)P.n, nb, px, f);
-  collide_pair<OP>(f, Fx, Fy, Fz, dS4, P, r, OP);
-#pragma unroll
-  for (int a = 0; a < 19; ++a) PairIO<S>::st2(g_out + (size_t)a * P.n + nb.self, a, f[a]);
+  fused_pair_at<S, OP, SIGMA>(g_in, g_out, psi, P, x, y, z, r);
 }
-
-// Pull through L2 only (the populations were written by other blocks during this launch).
-template <typename S> struct L2Load;
-template <> struct L2Load<float> {
-  static __device__ __forceinline__ float2 ld2(const float *p) { return __ldcg((const float2 *)p); }
-  static __device__ __forceinline__ float ld1(const float *p) { return __ldcg(p); }
-};
-template <> struct L2Load<__half> {
-  static __device__ __forceinline__ float2 ld2(const __half *p) {
-    return __half22float2(__ldcg((const __half2 *)p));
-  }
-  static __device__ __forceinline__ float ld1(const __half *p) { return __half2float(__ldcg(p)); }
-};
 
 template <typename S, int EOS, bool DF>
 __device__ __forceinline__ void psi_plane(const S *__restrict__ g, float *__restrict__ psi, const KParams &P,
                                           const Tiles &T, int t, int z, unsigned &e) {
   const int x = (t % T.nx_t) * 2 * TXP + 2 * threadIdx.x, y = (t / T.nx_t) * TYR + threadIdx.y;
   if (x >= P.nx || y >= P.ny) return;
-  const PairX px{x, x == 0 ? P.nx - 1 : x - 1, x + 2 >= P.nx ? x + 2 - P.nx : x + 2};
-  const Nbhd nb(x, y, z, P);
-  V2 f[19];
-#pragma unroll
-  for (int a = 0; a < 19; ++a) {
-    const S *rowp = g + (size_t)a * P.n + src_row(nb, a);
-    float2 v;
-    if (ex_of(a) == 0)
-      v = L2Load<S>::ld2(rowp + px.x);
-    else if (ex_of(a) > 0)
-      v = make_float2(L2Load<S>::ld1(rowp + px.xm1), L2Load<S>::ld1(rowp + px.x));
-    else
-      v = make_float2(L2Load<S>::ld1(rowp + px.x + 1), L2Load<S>::ld1(rowp + px.xp2));
-    f[a] = PairIO<S>::decode(v, a);
-  }
-  *(float2 *)(psi + nb.self) = psi_pair<EOS, DF>(drho_pair(f), P, e);
+  psi_pair_at_l2<S, EOS, DF>(g, psi, P, x, y, z, e);
 }
 
 // Block b works on z chunk b / per_chunk ([z0, z1), at least three planes) and
@@ -172,7 +116,7 @@ __global__ void __launch_bounds__(NTH, 7) lagged_kernel(const S *__restrict__ g_
   };
   auto psi_of = [&](int z, int z_wait) {  // psi(t+1) of plane z once the neighbours have done plane z_wait
     for (int t = t0; t < T.n; t += per_chunk) {
-      if (!wait_neighbours(flags, T, t, z_wait, nz, stamp)) e |= kErrTimeout;
+      if (!wait_neighbours(flags, T, t, z_wait, nz, stamp, P)) e |= kErrTimeout;
       psi_plane<S, EOS, DF>(g_out, psi_out, P, T, t, z, e);
     }
   };

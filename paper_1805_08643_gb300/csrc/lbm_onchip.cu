@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(NTH, 3)
       // staging buffer m % 3 last held plane m - 3 and psi slot m & 3 plane m - 4:
       // the collision of plane m - 3 is the last to read either, so wait for it
       // (the ((m - 4) / 3)-th release of buffer (m - 3) % 3)
-      if (m >= 4 && !mbar_wait(&empty[(m - 3) % NSTAGE], ((m - 4) / NSTAGE) & 1)) {
+      if (m >= 4 && !mbar_wait(&empty[(m - 3) % NSTAGE], ((m - 4) / NSTAGE) & 1, P.spin_limit)) {
         e |= kErrTimeout;
         break;
       }
@@ -149,10 +149,10 @@ __global__ void __launch_bounds__(NTH, 3)
     const bool owned = x0 + lx < P.nx && y0 + ly < P.ny;
     const int gx = wrapi(x0 + lx, P.nx), gy = wrapi(y0 + ly, P.ny), c = (ly + 1) * PX + lx + 2;
     const Rates<V2> r(P);
-    bool ok = mbar_wait(&full[0], 0) && mbar_wait(&full[1], 0);  // planes z0 - 1 and z0
+    bool ok = mbar_wait(&full[0], 0, P.spin_limit) && mbar_wait(&full[1], 0, P.spin_limit);  // planes z0 - 1 and z0
     for (int z = z0; z < z1 && ok; ++z) {
       const int m = z - z0 + 1;
-      if (!mbar_wait(&full[(m + 1) & 3], ((m + 1) >> 2) & 1)) {  // psi of plane z + 1
+      if (!mbar_wait(&full[(m + 1) & 3], ((m + 1) >> 2) & 1, P.spin_limit)) {  // psi of plane z + 1
         ok = false;
         break;
       }

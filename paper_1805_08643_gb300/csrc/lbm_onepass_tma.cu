@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(((BX + 2) * (BY + 2) + 31) / 32 * 32, 1)
   bool stored_last = false;
   for (int zz = z0 - 1; zz <= z1; ++zz) {
     const int s = zz & 1;
-    if (!mbar_wait(&bar[s], phase[s])) e |= kErrTimeout;
+    if (!mbar_wait(&bar[s], phase[s], P.spin_limit)) e |= kErrTimeout;
     phase[s] ^= 1u;
     float f[19];
     float *fs = fstar + s * SM::FSTAR;

@@ -126,4 +126,100 @@ __device__ __forceinline__ void force_collide_pair(V2 f[19], const V2 p[19], con
   collide_pair<OP>(f, Fx, Fy, Fz, dS4, P, r, op_rt);
 }
 
+// Loads through L2 only, for populations written by other blocks earlier in
+// the same launch (the non-coherent read-only path could hold stale lines).
+template <typename S> struct L2Load;
+template <> struct L2Load<float> {
+  static __device__ __forceinline__ float2 ld2(const float *p) { return __ldcg((const float2 *)p); }
+  static __device__ __forceinline__ float ld1(const float *p) { return __ldcg(p); }
+};
+template <> struct L2Load<__half> {
+  static __device__ __forceinline__ float2 ld2(const __half *p) { return __half22float2(__ldcg((const __half2 *)p)); }
+  static __device__ __forceinline__ float ld1(const __half *p) { return __half2float(__ldcg(p)); }
+};
+
+// The pair (x, x+1), x even, of row y in plane z with its periodic x neighbours.
+__device__ __forceinline__ PairX pair_x(const KParams &P, int x) {
+  return PairX{x, x == 0 ? P.nx - 1 : x - 1, x + 2 >= P.nx ? x + 2 - P.nx : x + 2};
+}
+
+// Fused pass of one pair as the two-pass fused kernel computes it (Eqs. 4-6,
+// 15, pull streaming of Eq. 5), with the force taken from psi before the
+// populations are pulled: the two sets of 19 pairs are never live together,
+// which keeps the registers of the single-pass kernels down.  The arithmetic
+// and its order are those of fused_pair_kernel, so the results are equal bit
+// for bit.
+template <typename S, int OP, bool SIGMA, bool FORCE_FIRST = true>
+__device__ __forceinline__ void fused_pair_at(const S *__restrict__ g_in, S *__restrict__ g_out,
+                                              const float *__restrict__ psi, const KParams &P, int x, int y, int z,
+                                              const Rates<V2> &r) {
+  const PairX px = pair_x(P, x);
+  const Nbhd nb(x, y, z, P);
+  V2 f[19];
+  // without FORCE_FIRST both sets of loads are issued before either is used
+  // (one memory round trip, more registers)
+  if (!FORCE_FIRST) pull_pair<S>(g_in, (unsigned)P.n, nb, px, f);
+  V2 Fx, Fy, Fz, dS4;
+  {
+    V2 p[19];
+    auto row3 = [&](int row, V2 &c, V2 &plus, V2 &minus) {
+      const float2 m = __ldg((const float2 *)(psi + row + px.x));
+      const float l = __ldg(psi + row + px.xm1), rr = __ldg(psi + row + px.xp2);
+      c = V2(m);
+      plus = V2(m.y, rr);
+      minus = V2(l, m.x);
+    };
+    auto row1 = [&](int row) { return V2(__ldg((const float2 *)(psi + row + px.x))); };
+    row3(nb.r00, p[0], p[1], p[2]);
+    row3(nb.rp0, p[3], p[7], p[10]);
+    row3(nb.rm0, p[4], p[9], p[8]);
+    row3(nb.r0p, p[5], p[11], p[14]);
+    row3(nb.r0m, p[6], p[13], p[12]);
+    p[15] = row1(nb.rpp);
+    p[16] = row1(nb.rmm);
+    p[17] = row1(nb.rpm);
+    p[18] = row1(nb.rmp);
+    force_pair<SIGMA>(p, P, Fx, Fy, Fz, dS4);
+  }
+  if (FORCE_FIRST) pull_pair<S>(g_in, (unsigned)P.n, nb, px, f);
+  collide_pair<OP>(f, Fx, Fy, Fz, dS4, P, r, OP);
+#pragma unroll
+  for (int a = 0; a < 19; ++a) PairIO<S>::st2(g_out + (size_t)a * P.n + nb.self, a, f[a]);
+}
+
+// psi of one pair from populations written earlier in the same launch (the
+// psi pass of psi_pair_kernel, pulls through L2).
+template <typename S, int EOS, bool DF>
+__device__ __forceinline__ void psi_pair_at_l2(const S *__restrict__ g, float *__restrict__ psi, const KParams &P,
+                                               int x, int y, int z, unsigned &e) {
+  const PairX px = pair_x(P, x);
+  const Nbhd nb(x, y, z, P);
+  V2 f[19];
+#pragma unroll
+  for (int a = 0; a < 19; ++a) {
+    const S *rowp = g + (size_t)a * P.n + src_row(nb, a);
+    float2 v;
+    if (ex_of(a) == 0)
+      v = L2Load<S>::ld2(rowp + px.x);
+    else if (ex_of(a) > 0)
+      v = make_float2(L2Load<S>::ld1(rowp + px.xm1), L2Load<S>::ld1(rowp + px.x));
+    else
+      v = make_float2(L2Load<S>::ld1(rowp + px.x + 1), L2Load<S>::ld1(rowp + px.xp2));
+    f[a] = PairIO<S>::decode(v, a);
+  }
+  *(float2 *)(psi + nb.self) = psi_pair<EOS, DF>(drho_pair(f), P, e);
+}
+
+// Cross-block signalling inside one launch: a release increment of a
+// completion counter (after a block barrier, by one thread: the barrier and the
+// fence make every thread's earlier stores visible first) and an acquire load.
+__device__ __forceinline__ void counter_release_add(int *c, int v) {
+  asm volatile("fence.acq_rel.gpu;\n\tred.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(c), "r"(v) : "memory");
+}
+__device__ __forceinline__ int counter_acquire(const int *c) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+  return v;
+}
+
 }  // namespace lbm

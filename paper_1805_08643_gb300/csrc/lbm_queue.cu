@@ -1,0 +1,253 @@
+// Single-pass time step on an ordered work list (FP32-arithmetic forms, D3Q19,
+// Nx even): one persistent launch per step runs both passes of the two-pass
+// step as interleaved work.
+//
+// Work item k is a pair of tile jobs (64 x 4 nodes of one plane, one node
+// pair per thread):
+//   fused job (z, tile): the fused pass (Eqs. 4-6 and 15, pull streaming of
+//     Eq. 5): reads f(t) and psi(t), writes f*(t); each warp then counts its
+//     row done;
+//   psi job (z', tile'): the psi pass of the next step: rho(t+1) from the
+//     pulled f*(t) (Eq. 6), the EOS, psi(t+1).  It needs the fused jobs of
+//     planes z'-1..z'+1 on the tile and its eight neighbours (periodic) and
+//     pulls their output through L2, where it still is.
+// The host builds the list (and checks it): fused jobs plane by plane; each
+// psi job in the first free item at least one wave of the grid (`grid` items)
+// after the last fused job it reads, so that by the time a block reaches it
+// those fused jobs were taken a round earlier and the wait is one poll.  Block b works through items b, b + grid, b + 2 grid, ...; the
+// launch is cooperative (every block resident), so the unfinished item with
+// the lowest index always has its block at it and waits only on earlier fused
+// jobs, which are finished: progress needs no timing assumption.  Waits are
+// bounded all the same (KParams::spin_limit; a wait that gives up sets
+// kErrTimeout and the launch still ends).
+//
+// What this buys over two launches: the psi jobs' FP64 EOS runs on the same
+// SMs while the fused jobs stream HBM, and the populations they pull come from
+// L2 (writer and reader are about two planes plus one wave of tiles apart): DRAM traffic per node is f(t) read and f*(t) written once plus psi
+// read and written once (2 x 19 x s + 8 bytes) against 3 x 19 x s + 8.  The
+// arithmetic and its order are those of the two-pass kernels, so the results
+// are equal bit for bit.
+//
+// Counters: done[z * T + tile] counts the rows of fused job (z, tile) finished
+// over all launches (each of the kRows warps adds one after its stores), so a
+// psi job of launch `stamp` waits for done >= kRows * stamp and nothing is
+// ever reset.
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+#include "lbm_pair.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int TXP = 32;          // pair columns of a tile: 64 nodes
+constexpr int kRows = 4;         // rows of a tile (one warp each)
+constexpr int NTH = TXP * kRows;
+constexpr int kMinBlocks = 6;    // resident blocks per SM the register budget is set for
+
+struct TileGeo {
+  int ntx, nty, T;  // tiles along x, along y, per plane
+};
+
+__host__ __device__ inline TileGeo tile_geo(const KParams &P) {
+  TileGeo g;
+  g.ntx = (P.nx + 2 * TXP - 1) / (2 * TXP);
+  g.nty = (P.ny + kRows - 1) / kRows;
+  g.T = g.ntx * g.nty;
+  return g;
+}
+
+// item: x = fused plane (or -1), y = its tile, z = psi plane (or -1), w = its tile
+template <typename S, int OP, bool SIGMA, int EOS, bool DF>
+__global__ void __launch_bounds__(NTH, kMinBlocks)
+    queue_kernel(const S *__restrict__ g_in, S *__restrict__ g_out, const float *__restrict__ psi_in,
+                 float *__restrict__ psi_out, const KParams P, const int4 *__restrict__ items, int nitems,
+                 int *__restrict__ done, int stamp, unsigned *__restrict__ err) {
+  const TileGeo G = tile_geo(P);
+  const int lane = threadIdx.x, row = threadIdx.y;
+  unsigned e = 0;
+#pragma unroll 1
+  for (int k = blockIdx.x; k < nitems; k += gridDim.x) {
+    const int4 it = __ldg(items + k);
+    if (it.x >= 0) {
+      int z = it.x, t = it.y;
+      asm volatile("" : "+r"(z), "+r"(t));  // keep the row offsets out of the registers across items
+      const int x = (t % G.ntx) * 2 * TXP + 2 * lane, y = (t / G.ntx) * kRows + row;
+      if (x < P.nx && y < P.ny) fused_pair_at<S, OP, SIGMA, false>(g_in, g_out, psi_in, P, x, y, z, Rates<V2>(P));
+      __syncwarp();
+      if (lane == 0) counter_release_add(done + z * G.T + t, 1);
+    }
+    if (it.z >= 0) {
+      int z = it.z, t = it.w;
+      asm volatile("" : "+r"(z), "+r"(t));
+      const int tx = t % G.ntx, ty = t / G.ntx;
+      bool ok = true;
+      if (lane < 27) {  // fused jobs of planes z-1..z+1 on the 3 x 3 tiles around (tx, ty)
+        int zz = z + lane / 9 - 1, xx = tx + lane % 3 - 1, yy = ty + (lane / 3) % 3 - 1;
+        zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
+        xx = xx < 0 ? xx + G.ntx : (xx >= G.ntx ? xx - G.ntx : xx);
+        yy = yy < 0 ? yy + G.nty : (yy >= G.nty ? yy - G.nty : yy);
+        const int *c = done + zz * G.T + yy * G.ntx + xx;
+        const int target = kRows * (stamp + P.wait_bias);
+        for (int n = 0; counter_acquire(c) < target; ++n) {
+          if (n >= P.spin_limit) {
+            ok = false;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      if (!__all_sync(0xffffffffu, ok)) e |= kErrTimeout;
+      const int x = tx * 2 * TXP + 2 * lane, y = ty * kRows + row;
+      if (x < P.nx && y < P.ny) psi_pair_at_l2<S, EOS, DF>(g_out, psi_out, P, x, y, z, e);
+    }
+  }
+  if (e) atomicOr(err, e);
+}
+
+template <typename S, int OP, bool SIGMA, int EOS, bool DF>
+cudaError_t launch_kernel(const KParams &P, const void *g_in, void *g_out, const void *psi_in, void *psi_out,
+                          const QueueState &q, int stamp, unsigned *err, cudaStream_t s) {
+  auto kern = queue_kernel<S, OP, SIGMA, EOS, DF>;
+  const S *gi = (const S *)g_in;
+  S *go = (S *)g_out;
+  const float *pi = (const float *)psi_in;
+  float *po = (float *)psi_out;
+  KParams Pc = P;
+  const int4 *items = q.items;
+  int nitems = q.nitems, *done = q.done;
+  void *args[] = {(void *)&gi,    (void *)&go,     (void *)&pi,   (void *)&po,    (void *)&Pc,
+                  (void *)&items, (void *)&nitems, (void *)&done, (void *)&stamp, (void *)&err};
+  return cudaLaunchCooperativeKernel((const void *)kern, dim3(q.grid), dim3(TXP, kRows), args, 0, s);
+}
+
+template <typename S, int OP, bool SIGMA>
+cudaError_t by_eos(const KParams &P, bool df, const void *g_in, void *g_out, const void *psi_in, void *psi_out,
+                   const QueueState &q, int stamp, unsigned *err, cudaStream_t s) {
+  switch (P.eos) {
+    case kEosCS:
+      return df ? launch_kernel<S, OP, SIGMA, kEosCS, true>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s)
+                : launch_kernel<S, OP, SIGMA, kEosCS, false>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
+    case kEosExp:
+      return df ? launch_kernel<S, OP, SIGMA, kEosExp, true>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s)
+                : launch_kernel<S, OP, SIGMA, kEosExp, false>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
+    default:
+      return launch_kernel<S, OP, SIGMA, kEosNone, false>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
+  }
+}
+
+template <typename S>
+cudaError_t by_op(const KParams &P, int op, bool sigma, bool df, const void *g_in, void *g_out, const void *psi_in,
+                  void *psi_out, const QueueState &q, int stamp, unsigned *err, cudaStream_t s) {
+  if (op == kNonOrth)
+    return sigma ? by_eos<S, kNonOrth, true>(P, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s)
+                 : by_eos<S, kNonOrth, false>(P, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
+  return sigma ? by_eos<S, kOrth, true>(P, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s)
+               : by_eos<S, kOrth, false>(P, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
+}
+
+// Resident blocks per SM of the kernels a context launches: the smallest over
+// the instantiations of the storage type, so that a cooperative launch of
+// that many blocks per SM fits whichever one runs.
+template <typename S>
+cudaError_t occupancy_of(int *per_sm) {
+  using K = void (*)(const S *, S *, const float *, float *, const KParams, const int4 *, int, int *, int, unsigned *);
+  const K ks[] = {queue_kernel<S, kNonOrth, true, kEosCS, false>, queue_kernel<S, kOrth, true, kEosCS, false>,
+                  queue_kernel<S, kNonOrth, false, kEosCS, true>, queue_kernel<S, kOrth, false, kEosExp, false>};
+  int m = 1 << 30;
+  for (K k : ks) {
+    int v = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k, NTH, 0);
+    if (e != cudaSuccess) return e;
+    m = std::min(m, v);
+  }
+  *per_sm = m;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+bool queue_supported(const KParams &P, int precision) { return precision != kF64 && P.nx % 2 == 0 && P.q == 19; }
+
+cudaError_t queue_grid(int precision, int *grid) {
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaError_t e = precision == kF32 ? occupancy_of<float>(&per_sm) : occupancy_of<__half>(&per_sm);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  *grid = per_sm * sms;
+  return cudaSuccess;
+}
+
+size_t queue_counters(const KParams &P) { return (size_t)P.nz * tile_geo(P).T; }
+
+bool queue_items(const KParams &P, int grid, std::vector<int4> &out) {
+  const TileGeo G = tile_geo(P);
+  const long long nf = (long long)P.nz * G.T;
+  if (P.nz < 3 || grid < 1 || nf >= (1LL << 30)) return false;
+  // fused job j = (j / T, j % T); psi job (z, t) is ready after the last of the
+  // 27 fused jobs it reads and goes to the first free item >= ready + lag: one
+  // wave of the grid later, so its block reaches it a round after the last of
+  // those fused jobs was taken
+  const long long lag = grid;
+  std::vector<long long> ready((size_t)nf);
+  for (long long p = 0; p < nf; ++p) {
+    const int z = (int)(p / G.T), t = (int)(p % G.T), tx = t % G.ntx, ty = t / G.ntx;
+    long long r = -1;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int zz = (z + dz + P.nz) % P.nz, yy = (ty + dy + G.nty) % G.nty, xx = (tx + dx + G.ntx) % G.ntx;
+          r = std::max(r, (long long)zz * G.T + yy * G.ntx + xx);
+        }
+    ready[p] = r;
+  }
+  std::vector<long long> order((size_t)nf);
+  for (long long p = 0; p < nf; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(), [&](long long a, long long b) { return ready[a] < ready[b]; });
+  out.assign((size_t)nf, make_int4(-1, -1, -1, -1));
+  for (long long j = 0; j < nf; ++j) out[j] = make_int4((int)(j / G.T), (int)(j % G.T), -1, -1);
+  long long next = 0;  // first item that may still take a psi job
+  for (long long p : order) {
+    const long long k = std::max(next, ready[p] + lag);
+    while ((long long)out.size() <= k) out.push_back(make_int4(-1, -1, -1, -1));
+    out[k].z = (int)(p / G.T);
+    out[k].w = (int)(p % G.T);
+    next = k + 1;
+  }
+  if ((long long)out.size() >= (1LL << 31)) return false;
+  // check: every job once; each psi job in an item after the fused jobs it reads
+  std::vector<char> fseen((size_t)nf, 0), pseen((size_t)nf, 0);
+  for (size_t k = 0; k < out.size(); ++k) {
+    const int4 it = out[k];
+    if (it.x >= 0) {
+      const long long j = (long long)it.x * G.T + it.y;
+      if (j != (long long)k || fseen[j]) return false;
+      fseen[j] = 1;
+    }
+    if (it.z >= 0) {
+      if (it.z >= P.nz || it.w < 0 || it.w >= G.T) return false;
+      const long long p = (long long)it.z * G.T + it.w;
+      if (pseen[p] || ready[p] >= (long long)k) return false;
+      pseen[p] = 1;
+    }
+  }
+  for (long long p = 0; p < nf; ++p)
+    if (!fseen[p] || !pseen[p]) return false;
+  return true;
+}
+
+cudaError_t launch_queue(const KParams &P, int precision, int op, bool sigma, bool df, const void *g_in, void *g_out,
+                         const void *psi_in, void *psi_out, const QueueState &q, int stamp, unsigned *err,
+                         cudaStream_t s) {
+  if (!queue_supported(P, precision)) return cudaErrorInvalidValue;
+  if (precision == kF32) return by_op<float>(P, op, sigma, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
+  return by_op<__half>(P, op, sigma, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
+}
+
+}  // namespace lbm

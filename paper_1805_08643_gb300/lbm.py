@@ -60,6 +60,7 @@ SIGNATURES = {
     "lbm_kernel_times": (_c_int, [_vp, _dp, _llp, _dp, _llp]),
     "lbm_set_tuning": (_c_int, [_vp, _c_int, _c_int, _c_int]),
     "lbm_set_eos_arith": (_c_int, [_vp, _c_int]),
+    "lbm_set_wait_budget": (_c_int, [_vp, _c_int, _c_int]),
     "lbm_set_variable_viscosity": (_c_int, [_vp, _c_double, _c_double, _c_double, _c_double]),
     "lbm_get_tuning": (_c_int, [_vp, ctypes.POINTER(_c_int), ctypes.POINTER(_c_int), ctypes.POINTER(_c_int)]),
     "lbm_step_count": (ctypes.c_longlong, [_vp]),
@@ -265,15 +266,22 @@ class Lattice:
     def set_tuning(self, single_pass=True, tile=1, z_planes=0):
         """single_pass: False / True (register-prefetch kernel) / "tma" (bulk-copy kernel) /
         "onchip" (psi evaluated on chip by producer warps; Nx even) / "lagged" (the next psi pass one plane
-        behind the fused pass in one cooperative launch; Nx even)."""
+        behind the fused pass in one cooperative launch; Nx even) / "queue" (fused and next-psi items of
+        row bands from an ordered work queue in one persistent launch; Nx even, D3Q19)."""
         if isinstance(single_pass, str):
-            modes = {"tma": 2, "onchip": 3, "lagged": 4}
+            modes = {"tma": 2, "onchip": 3, "lagged": 4, "queue": 5}
             if single_pass not in modes:
                 raise ValueError(f"unknown single_pass mode {single_pass!r}")
             mode = modes[single_pass]
         else:
             mode = int(bool(single_pass))
         self._check(lib.lbm_set_tuning(self._h, mode, int(tile), int(z_planes)), "lbm_set_tuning")
+
+    def set_wait_budget(self, spin_limit=0, inject_unreachable=False):
+        """Polls before a device-side wait gives up (0: the default); inject_unreachable makes the cross-block
+        waits of the "lagged" and "queue" modes wait for a count no block reaches (a test of the timeout path)."""
+        self._check(lib.lbm_set_wait_budget(self._h, int(spin_limit), 1 if inject_unreachable else 0),
+                    "lbm_set_wait_budget")
 
     def set_variable_viscosity(self, rho_l, rho_v, nu_l, nu_v):
         """nu linear in rho between (rho_v, nu_v) and (rho_l, nu_l), clamped; nu_l = nu_v = 0 switches it off."""
@@ -286,7 +294,8 @@ class Lattice:
     def tuning(self):
         sp, t, z = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         self._check(lib.lbm_get_tuning(self._h, ctypes.byref(sp), ctypes.byref(t), ctypes.byref(z)), "lbm_get_tuning")
-        return {"single_pass": {0: False, 1: True, 2: "tma", 3: "onchip", 4: "lagged"}[sp.value], "tile": t.value,
+        return {"single_pass": {0: False, 1: True, 2: "tma", 3: "onchip", 4: "lagged", 5: "queue"}[sp.value],
+                "tile": t.value,
                 "z_planes": z.value}
 
     def set_profiling(self, on=True):
