@@ -11,15 +11,20 @@ model settles to: a W = 5 profile leaves a shell that relaxes by sending a
 converging density wave into the droplet, which focuses at the centre of an
 R = 40 droplet and makes the run non-finite after about 55 steps (FP64
 included); with W = 3 all forms run the 1000 steps.  The headline line is
-the non-orthogonal operator with FP32 arithmetic and storage; the ``forms``
-object adds both operators in FP64 and FP32 and the FP16-storage form, the
-D3Q15 variant of the non-orthogonal operator in the same three precisions, all
-on the same box, and the batched and served forms.  A "step" is one lattice
-time step (psi pass + fused pass) over the whole box; MLUPS = 1e-6 * nodes *
-steps / second.
+the non-orthogonal operator with FP32 arithmetic and storage, stepped as the
+library steps it by default: one launch per step of the work-list single pass
+(the fused pass and the next step's psi pass as interleaved tile jobs).  The
+``forms`` object adds both operators in FP64, FP32 (also as the two-pass step)
+and FP16 storage, the D3Q15 variant of the non-orthogonal operator in the same
+three precisions, all on the same box, and the batched and served forms.  A
+"step" is one lattice time step over the whole box; MLUPS = 1e-6 * nodes *
+steps / second.  Timing: the median of --repeats regions of --steps steps, each
+bracketed by CUDA events on the launch stream with nothing else recorded inside
+(the kernel split comes from a separate region with per-launch events).
 
-  python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--forms headline|batched|all]
-                  [--op nonorth|orth|nonorth_d3q15] [--prec f64|f32|f16]
+  python bench.py [--gpus N --steps K --warmup W --repeats R] [--impl reference]
+                  [--forms headline|batched|all] [--op nonorth|orth|nonorth_d3q15] [--prec f64|f32|f16]
+                  [--mode default|two-pass|queue|lagged|onchip|single|tma]
 
 Under torchrun (N > 1) each rank runs its own box on its own GPU (replicas,
 weak scaling); the timed region is bracketed by barriers and the max over
@@ -61,10 +66,16 @@ PSI_BYTES = {"f64": 19 * 8 + 8, "f32": 19 * 4 + 4, "f16": 19 * 2 + 4}
 # the same for the D3Q15 variant (15 populations per node)
 FUSED_BYTES_Q15 = {"f64": 15 * 8 * 2 + 8, "f32": 15 * 4 * 2 + 4, "f16": 15 * 2 * 2 + 4}
 PSI_BYTES_Q15 = {"f64": 15 * 8 + 8, "f32": 15 * 4 + 4, "f16": 15 * 2 + 4}
+# minimum bytes per lattice update: populations read and written once, psi read and written once
+STEP_MIN_BYTES = {"f64": 19 * 8 * 2 + 16, "f32": 19 * 4 * 2 + 8, "f16": 19 * 2 * 2 + 8}
+STEP_MIN_BYTES_Q15 = {"f64": 15 * 8 * 2 + 16, "f32": 15 * 4 * 2 + 8, "f16": 15 * 2 * 2 + 8}
 HEADLINE = ("nonorth", "f32")
 # DRAM bytes per node of the fused pass, from one ncu capture of the current kernel at 256^3 (dram__bytes_read
 # + dram__bytes_write over the nodes); null for forms without such a capture.
 FUSED_DRAM_BYTES = {("nonorth", "f32"): 152.6, ("nonorth", "f16"): 77.4}
+# DRAM bytes per node of one launch of the work-list single pass at 256^3 (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch over the nodes)
+QUEUE_DRAM_BYTES = {}
 # FP64 instructions per node of the fused pass (ncu instruction counts at 128^3 over the nodes) and the FP64
 # issue peak of one GB300: 2 per SM per clock x 152 SMs x 2070 MHz.
 FUSED_FP64_INSTR = {"nonorth": 255.0, "orth": 309.0, "nonorth_d3q15": 207.0}
@@ -193,14 +204,21 @@ def make_lattice(op, prec, edge, sigma=SIGMA_DROPLET):
     return lat, rl, rv
 
 
-def time_form(op, prec, edge, steps, warmup, world, clocks_index=None, field="droplet", single_pass=False,
-              eos_arith="f64"):
-    """Device-timed steps of one form; returns (ms_per_step, kernel times, clocks)."""
+MODES = {"default": None, "two-pass": 0, "single": 1, "tma": "tma", "onchip": "onchip", "lagged": "lagged",
+         "queue": "queue"}
+
+
+def time_form(op, prec, edge, steps, warmup, world, clocks_index=None, field="droplet", mode="default",
+              eos_arith="f64", repeats=5):
+    """Device time of one form: `repeats` regions of `steps` steps each (CUDA events on the launch stream,
+    nothing else recorded inside them; barrier + synchronize around each), median per step; then, outside
+    those regions, one region of the same steps with per-launch events for the kernel split."""
     import torch
 
     lat, rl, rv = make_lattice(op, prec, edge, SIGMA_DROPLET if field == "droplet" else SIGMA_FLAT)
-    if single_pass:
-        lat.set_tuning({1: True, 2: "tma", 3: "onchip", 4: "lagged"}[int(single_pass)], 1, 0)
+    if MODES[mode] is not None:
+        m = MODES[mode]
+        lat.set_tuning(m if isinstance(m, str) else bool(m), 1, 0)
     if eos_arith != "f64":
         lat.set_eos_arith(eos_arith)
     if field == "droplet":
@@ -208,27 +226,36 @@ def time_form(op, prec, edge, steps, warmup, world, clocks_index=None, field="dr
     else:
         lat.init_flat(2, edge / 4, 3 * edge / 4, W_FLAT, rl, rv)
     lat.step(warmup)
-    lat.set_profiling(True)
-    lat.kernel_times()  # reset
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = Clocks(clocks_index) if clocks_index is not None else None
+    times = []
     barrier(world)
     torch.cuda.synchronize()
-    clk = Clocks(clocks_index) if clocks_index is not None else None
     if clk:
         clk.__enter__()
-    e0.record(stream)
-    lat.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        lat.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        times.append(e0.elapsed_time(e1))
     if clk:
         clk.__exit__()
-    barrier(world)
-    ms = e0.elapsed_time(e1)
-    kt = lat.kernel_times()
     status = lat.check()
+    # kernel split, from a separate region with per-launch events
+    lat.set_profiling(True)
+    lat.kernel_times()
+    lat.step(steps)
+    kt = lat.kernel_times()
+    lat.set_profiling(False)
+    tuning = lat.tuning()
     lat.close()
-    return ms, kt, (clk.summary() if clk else None), status
+    return {"ms": statistics.median(times), "region_ms": times, "kt": kt, "clocks": clk.summary() if clk else None,
+            "status": status, "single_pass": tuning["single_pass"]}
 
 
 def e2e_run(op, prec, edge, steps):
@@ -431,62 +458,223 @@ def oracle_for(op):
     return L, op
 
 
-def oracle_slab(op, nz):
-    """Oracle state of the nz-plane slab through the centre of the 256^3 droplet box (periodic in z)."""
+def oracle_slab(op, nz, edge=EDGE, z0=None):
+    """Oracle state of the nz planes [z0, z0 + nz) of the edge^3 droplet box (default: through its centre),
+    run as a box of its own (periodic in z): a timing sample whose work per node is the full box's."""
     from oracle import lbm_oracle as L
     from oracle import maxwell
 
     O, oop = oracle_for(op)
     Tc = L.critical_temperature(A, B, R_GAS)
     rl, rv = maxwell.coexistence_cs(T_OVER_TC, A, B, R_GAS)
-    p = L.Params(grid=(EDGE, EDGE, nz), operator=oop, a=A, b=B, R=R_GAS, T=T_OVER_TC * Tc, G=G,
+    p = L.Params(grid=(edge, edge, nz), operator=oop, a=A, b=B, R=R_GAS, T=T_OVER_TC * Tc, G=G,
                  sigma=SIGMA_DROPLET, **RATES)
-    rho = L.droplet_density((EDGE, EDGE, EDGE), (EDGE / 2,) * 3, 40.0, W_HEADLINE, rl, rv)[EDGE // 2 - nz // 2:EDGE // 2 + nz // 2]
+    if z0 is None:
+        z0 = edge // 2 - nz // 2
+    rho = slab_density(edge, z0, nz, 40.0 * edge / 256, W_HEADLINE, rl, rv)
     return O, p, O.equilibrium_state(p, rho)
 
 
-def cpu_baseline(op=None, seconds_target=15.0):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload."""
-    op = op or HEADLINE[0]
-    nz = 8
-    O, p, f = oracle_slab(op, nz)
-    steps = 0
+def slab_density(edge, z0, nz, R, W, rl, rv):
+    """Planes [z0, z0 + nz) of the Eq. 59 droplet centred in the edge^3 box (periodic minimum-image
+    distances over the full box), computed for the slab alone (no full-box array)."""
+    c = edge / 2
+
+    def d(v):
+        a = np.abs(v - c)
+        return np.minimum(a, edge - a)
+
+    x = d(np.arange(edge, dtype=np.float64))
+    z = d(np.arange(z0, z0 + nz, dtype=np.float64))
+    r = np.sqrt(z[:, None, None] ** 2 + x[None, :, None] ** 2 + x[None, None, :] ** 2)
+    return 0.5 * (rl + rv) - 0.5 * (rl - rv) * np.tanh(2.0 * (r - R) / W)
+
+
+def _oracle_job(job):
+    """One CPU-baseline task (in a spawned process): build its oracle state, time `steps` steps of it."""
+    kind, op, edge, nz, z0, steps = job
+    if kind == "parity":  # the 32^3 parity workload: T = 0.8 T_c, droplet R = 8, W = 2, no Eq. 16 term
+        from oracle import lbm_oracle as L
+        from oracle import maxwell
+
+        O, oop = oracle_for(op)
+        Tc = L.critical_temperature(A, B, R_GAS)
+        rl, rv = maxwell.coexistence_cs(0.8, A, B, R_GAS)
+        p = L.Params(grid=(edge,) * 3, operator=oop, a=A, b=B, R=R_GAS, T=0.8 * Tc, G=G, s_e=1.1, s_nu=1.0,
+                     s_q=1.1, s_pi=1.1, s_eps=1.1, s_m=1.1)
+        f = O.equilibrium_state(p, L.droplet_density((edge,) * 3, (edge / 2,) * 3, 8.0, 2.0, rl, rv))
+        nodes = edge ** 3
+    else:
+        O, p, f = oracle_slab(op, nz, edge, z0)
+        nodes = edge * edge * nz
     t0 = time.perf_counter()
-    while True:
+    for _ in range(steps):
         f = O.step(p, f)
-        steps += 1
-        if time.perf_counter() - t0 > seconds_target:
-            break
-    dt = time.perf_counter() - t0
-    nodes = EDGE * EDGE * nz
-    return {"value": nodes * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{EDGE}x{EDGE}x{nz} slab through the droplet centre, {steps} FP64 steps, "
-                      f"{lattice_name(op)} {op} operator, single-threaded numpy"}
+    return nodes * steps, time.perf_counter() - t0
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(op=None):
+    """The FP64 oracle, as it stands (single-threaded numpy per process), on the host's cores.
+
+    Samples (about 15-20 s of CPU work on 16 Grace cores):
+      * all cores, 256^3 x 10 steps: as many nodes as the whole headline box, as `cores` copies of the
+        256 x 256 x (256 / cores) slab through the droplet centre, one process each (the line's value);
+      * all cores, 512^3 x 2 steps: the same at 512^3 (R = 80), 4 x `cores` copies of a centre slab of 8 planes;
+      * all cores, 32^3 x 200 steps: the parity workload, one full copy per process;
+      * one core: 256 x 256 x 8 slab through the droplet centre, 3 steps.
+    A slab runs as a periodic box of its own, so its work per node is the full box's; centred on the
+    droplet, its periodic seam joins two planes at about the same distance from the centre (slabs cut
+    elsewhere would join liquid to vapour across the seam and leave the EOS domain within steps).
+    Processes are spawned (no fork after CUDA initialisation)."""
+    import multiprocessing as mp
+
+    op = op or HEADLINE[0]
+    cores = cpu_cores()
+    ctx = mp.get_context("spawn")
+    out = {}
+
+    def run(name, jobs, procs, what):
+        t0 = time.perf_counter()
+        with ctx.Pool(procs) as pool:
+            res = pool.map(_oracle_job, jobs, chunksize=1)
+        wall = time.perf_counter() - t0
+        lups = sum(r[0] for r in res)
+        out[name] = {"value": lups / wall / 1e6, "unit": UNIT, "cores": procs, "seconds": wall, "sample": what}
+
+    n256 = max(1, min(cores, EDGE))
+    nz256 = EDGE // n256
+    run("256^3x10", [("slab", op, EDGE, nz256, None, 10) for _ in range(n256)], n256,
+        f"{EDGE}^3 nodes x 10 FP64 oracle steps: {n256} copies of the periodic {EDGE}x{EDGE}x{nz256} slab through "
+        f"the droplet centre, in {n256} spawned processes")
+    n512 = 4 * n256
+    run("512^3x2", [("slab", op, 512, 512 // n512, None, 2) for _ in range(n512)], n256,
+        f"512^3 nodes x 2 FP64 oracle steps: {n512} copies of the periodic 512x512x{512 // n512} slab through the "
+        f"centre of the 512^3 droplet box (R=80), on {n256} processes")
+    run("32^3x200", [("parity", op, 32, 32, 0, 200) for _ in range(n256)], n256,
+        f"the 32^3 parity workload (T=0.8Tc, R=8, W=2), 200 FP64 oracle steps, one full copy per process, "
+        f"{n256} processes")
+    run("1core", [("slab", op, EDGE, 8, None, 3)], 1,
+        f"{EDGE}x{EDGE}x8 slab through the droplet centre, 3 FP64 oracle steps, one process")
+    head = out["256^3x10"]
+    return {"value": head["value"], "unit": UNIT, "cores": head["cores"], "kind": "oracle",
+            "sample": head["sample"] + f" ({lattice_name(op)} {op} operator, single-threaded numpy per process)",
+            "samples": out}
+
+
+class _SlabWorker:
+    """A spawned process that holds one oracle slab and steps it on request (reference arm)."""
+
+    def __init__(self, ctx, op, nz, z0):
+        self.conn, child = ctx.Pipe()
+        self.proc = ctx.Process(target=_slab_worker_main, args=(child, op, nz, z0), daemon=True)
+        self.proc.start()
+
+    def close(self):
+        try:
+            self.conn.send(None)
+        except Exception:
+            pass
+        self.proc.join(timeout=30)
+
+
+def _slab_worker_main(conn, op, nz, z0):
+    O, p, f = oracle_slab(op, nz, EDGE, z0)
+    conn.send("ready")
+    while True:
+        msg = conn.recv()
+        if msg is None:
+            return
+        f = O.step(p, f)
+        conn.send(1)
 
 
 def reference_arm(args, world, rank):
+    """The oracle on the host cores, on this benchmark's workload: every step, one FP64 oracle step of
+    `cores` periodic z-slabs of 256 x 256 x 2 around the droplet centre, one spawned process each."""
     if rank != 0:
         return
-    nz = 2  # one step of this slab takes about 50 ms: the default 1000 steps end within a minute
-    O, p, f = oracle_slab(args.op, nz)
-    for _ in range(args.warmup):
-        f = O.step(p, f)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        f = O.step(p, f)
-    dt = time.perf_counter() - t0
-    nodes = EDGE * EDGE * nz
+    import multiprocessing as mp
+
+    cores = cpu_cores()
+    nz = 2
+    ctx = mp.get_context("spawn")
+    z_lo = EDGE // 2 - cores * nz // 2
+    workers = [_SlabWorker(ctx, args.op, nz, max(0, z_lo + k * nz) % (EDGE - nz + 1)) for k in range(cores)]
+    try:
+        for w in workers:
+            assert w.conn.recv() == "ready"
+
+        def step():
+            for w in workers:
+                w.conn.send(1)
+            for w in workers:
+                w.conn.recv()
+
+        for _ in range(args.warmup):
+            step()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step()
+        dt = time.perf_counter() - t0
+    finally:
+        for w in workers:
+            w.close()
+    nodes = EDGE * EDGE * nz * cores
     v = nodes * args.steps / dt / 1e6
-    sample = f"each step: one FP64 oracle step of the {EDGE}x{EDGE}x{nz} slab through the droplet centre"
+    sample = (f"each step: one FP64 oracle step (numpy, as it stands) of each of {cores} periodic "
+              f"{EDGE}x{EDGE}x{nz} z-slabs of the {EDGE}^3 droplet box, one spawned process per core")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": workload_text(args.op, args.prec, EDGE), "edge": EDGE,
-                                        "operator": args.op, "precision": args.prec, "parallelism": "single"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": {"workload": reference_workload_text(args.op, cores, nz), "edge": EDGE,
+                                        "operator": args.op, "precision": "f64", "parallelism": f"{cores} host processes"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+def reference_workload_text(op, cores, nz):
+    op_text = {"nonorth": "non-orthogonal", "orth": "orthogonal", "nonorth_d3q15": "non-orthogonal"}[op]
+    return (f"{lattice_name(op)} {op_text} MRT + CS pseudopotential, droplet R=40 W=3 of the {EDGE}^3 periodic box, "
+            f"T=0.7Tc, sigma=0.105 (Eq. 16); the FP64 oracle on {cores} z-slabs of {EDGE}x{EDGE}x{nz} per step "
+            f"(FP64 compute and storage)")
+
+
+def form_entry(op, prec, edge, steps, warmup, world, hbm_peak, mode="default", field="droplet", eos_arith="f64",
+               repeats=3):
+    """One line of the `forms` object: throughput, whole-step bandwidth against the minimum bytes per update,
+    and the kernel split."""
+    r = time_form(op, prec, edge, steps, warmup, world, field=field, mode=mode, eos_arith=eos_arith, repeats=repeats)
+    n = edge ** 3
+    q15 = op == "nonorth_d3q15"
+    fb = (FUSED_BYTES_Q15 if q15 else FUSED_BYTES)[prec]
+    pb = (PSI_BYTES_Q15 if q15 else PSI_BYTES)[prec]
+    smin = (STEP_MIN_BYTES_Q15 if q15 else STEP_MIN_BYTES)[prec]
+    ms_step = r["ms"] / steps
+    kt = r["kt"]
+    f_ms = kt["fused_ms"] / max(kt["fused_launches"], 1)
+    e = {"mlups": n * steps / (r["ms"] / 1e3) / 1e6, "ms_per_step": ms_step,
+         "step": "work-list single pass (one launch)" if r["single_pass"] == "queue" else
+                 ("two-pass (psi pass + fused pass)" if not r["single_pass"] else f"single pass ({r['single_pass']})"),
+         "bytes_per_lup_min": smin, "whole_step_gbs_at_min_bytes": smin * n / (ms_step / 1e3) / 1e9,
+         "whole_step_frac_of_hbm": smin * n / (ms_step / 1e3) / 1e9 / hbm_peak, "status": r["status"]}
+    if not r["single_pass"]:
+        p_ms = kt["psi_ms"] / max(kt["psi_launches"], 1)
+        e.update({"fused_ms": f_ms, "psi_ms": p_ms, "fused_gbs": fb * n / (f_ms / 1e3) / 1e9,
+                  "hbm_frac_fused": fb * n / (f_ms / 1e3) / 1e9 / hbm_peak, "bytes_per_lup_two_pass": fb + pb})
+    if prec == "f64" and op in FUSED_FP64_INSTR:
+        e["fp64_alu_frac_fused"] = FUSED_FP64_INSTR[op] * n / (f_ms / 1e3) / 1e9 / FP64_PEAK_GINSTR
+    if eos_arith != "f64":
+        e["note"] = "EOS radicand in compensated FP32 pairs instead of FP64"
+    return e
 
 
 def main():
@@ -494,13 +682,14 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--repeats", type=int, default=5, help="timed regions of --steps steps; the median is reported")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--edge", type=int, default=EDGE)
     ap.add_argument("--op", default=HEADLINE[0], choices=["nonorth", "orth", "nonorth_d3q15"])
     ap.add_argument("--prec", default=HEADLINE[1], choices=["f64", "f32", "f16"])
-    ap.add_argument("--single-pass", type=int, default=0,
-                    help="1: single-pass kernel, 2: its bulk-copy variant, 3: on-chip-psi single pass, "
-                         "4: trailing-psi single pass (FP32 arithmetic)")
+    ap.add_argument("--mode", default="default", choices=sorted(MODES),
+                    help="step kernels: the library default (work-list single pass for FP32 storage, two-pass "
+                         "otherwise), or one of the lbm_set_tuning modes")
     ap.add_argument("--forms", default="all", help="'all', 'headline' or 'batched' (headline + batched + served)")
     ap.add_argument("--batch-boxes", type=int, default=512, help="boxes of the batched form")
     ap.add_argument("--no-cpu", action="store_true")
@@ -513,6 +702,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    args.repeats = max(1, args.repeats)
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         reference_arm(args, world, rank)
@@ -536,84 +726,67 @@ def main():
     hbm_peak, peak_kind = peaks()
 
     op, prec = args.op, args.prec
-    ms, kt, clocks, status = time_form(op, prec, args.edge, args.steps, args.warmup, world, clocks_index=local,
-                                       single_pass=args.single_pass, eos_arith=args.eos_arith)
-    ms = max_over_ranks(ms, world)
+    r = time_form(op, prec, args.edge, args.steps, args.warmup, world, clocks_index=local, mode=args.mode,
+                  eos_arith=args.eos_arith, repeats=args.repeats)
+    ms = max_over_ranks(r["ms"], world)  # median region of this rank, max over ranks
     ms_step = ms / args.steps
     value = sum_over_ranks(n * args.steps / (ms / 1e3) / 1e6, world)  # all ranks' nodes / max time
+    kt = r["kt"]
     fused_ms = kt["fused_ms"] / max(kt["fused_launches"], 1)
     psi_ms = kt["psi_ms"] / max(kt["psi_launches"], 1)
-    fused_bytes = (FUSED_BYTES_Q15 if op == "nonorth_d3q15" else FUSED_BYTES)[prec]
-    achieved = fused_bytes * n / (fused_ms / 1e3) / 1e9
+    q15 = op == "nonorth_d3q15"
+    smin = (STEP_MIN_BYTES_Q15 if q15 else STEP_MIN_BYTES)[prec]
+    single = r["single_pass"]
 
     if prec == "f64" and op in FUSED_FP64_INSTR:
         ach = FUSED_FP64_INSTR[op] * n / (fused_ms / 1e3) / 1e9
         roofline = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_GINSTR, "unit": "G FP64 instr/s",
-                    "frac": ach / FP64_PEAK_GINSTR, "traffic": None, "peak_kind": "derived: 2 FP64/SM/clk x 152 x 2070 MHz",
+                    "frac": ach / FP64_PEAK_GINSTR, "traffic": None,
+                    "peak_kind": "derived: 2 FP64/SM/clk x 152 x 2070 MHz",
                     "kernel": "fused force+collide+stream", "fp64_instr_per_node": FUSED_FP64_INSTR[op],
                     "fused_ms": fused_ms, "psi_ms": psi_ms}
-    else:
-        dram = FUSED_DRAM_BYTES.get((op, prec)) if args.edge == EDGE and not args.single_pass else None
+        launches = 2 * args.steps
+    elif single == "queue":
+        # one launch per step: the kernel's average launch duration is the step time
+        achieved = smin * n / (ms_step / 1e3) / 1e9
+        dram = QUEUE_DRAM_BYTES.get((op, prec)) if args.edge == EDGE else None
         roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": achieved / hbm_peak, "traffic": dram * n if dram else None,
-                    "peak_kind": peak_kind, "kernel": "single pass" if args.single_pass else "fused force+collide+stream",
+                    "frac": achieved / hbm_peak, "traffic": dram * n if dram else None, "peak_kind": peak_kind,
+                    "kernel": "work-list single pass (fused pass + next step's psi pass, one launch per step)",
+                    "bytes_per_node": smin, "kernel_ms": ms_step,
+                    "kernel_ms_profiled": fused_ms}
+        launches = args.steps
+    else:
+        fused_bytes = (FUSED_BYTES_Q15 if q15 else FUSED_BYTES)[prec]
+        achieved = fused_bytes * n / (fused_ms / 1e3) / 1e9
+        dram = FUSED_DRAM_BYTES.get((op, prec)) if args.edge == EDGE and not single else None
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": achieved / hbm_peak, "traffic": dram * n if dram else None, "peak_kind": peak_kind,
+                    "kernel": f"single pass ({single})" if single else "fused force+collide+stream",
                     "bytes_per_node": fused_bytes, "fused_ms": fused_ms, "psi_ms": psi_ms}
+        launches = args.steps if single else 2 * args.steps
+    whole = {"bytes_per_lup_min": smin, "gbs_at_min_bytes": smin * n / (ms_step / 1e3) / 1e9,
+             "frac_of_hbm": smin * n / (ms_step / 1e3) / 1e9 / hbm_peak}
+
     forms = {}
     if args.forms == "all":
+        E = args.edge
+        K, W = args.steps, args.warmup
+        k64 = max(10, K // 8)
         for fop in ("nonorth", "orth"):
             for fprec in ("f64", "f32", "f16"):
-                steps_f = max(10, args.steps // (8 if fprec == "f64" else 1))
-                fms, fkt, _, fst = time_form(fop, fprec, args.edge, steps_f, args.warmup, world)
-                f_fused = fkt["fused_ms"] / max(fkt["fused_launches"], 1)
-                f_psi = fkt["psi_ms"] / max(fkt["psi_launches"], 1)
-                step_bytes = (FUSED_BYTES[fprec] + PSI_BYTES[fprec]) * n
-                extra = {}
-                if fprec == "f64":
-                    extra["fp64_alu_frac_fused"] = FUSED_FP64_INSTR[fop] * n / (f_fused / 1e3) / 1e9 / FP64_PEAK_GINSTR
-                forms[f"{fop}_{fprec}_droplet"] = {**extra,
-                    "mlups": n * steps_f / (fms / 1e3) / 1e6,
-                    "ms_per_step": fms / steps_f,
-                    "fused_ms": f_fused, "psi_ms": f_psi,
-                    "fused_gbs": FUSED_BYTES[fprec] * n / (f_fused / 1e3) / 1e9,
-                    "step_gbs": step_bytes / (fms / steps_f / 1e3) / 1e9,
-                    "hbm_frac_fused": FUSED_BYTES[fprec] * n / (f_fused / 1e3) / 1e9 / hbm_peak,
-                    "bytes_per_lup_two_pass": FUSED_BYTES[fprec] + PSI_BYTES[fprec],
-                    "status": fst,
-                }
-
+                forms[f"{fop}_{fprec}_droplet"] = form_entry(fop, fprec, E, k64 if fprec == "f64" else K, W, world,
+                                                             hbm_peak)
+            forms[f"{fop}_f32_droplet_two_pass"] = form_entry(fop, "f32", E, K, W, world, hbm_peak, mode="two-pass")
         for fprec in ("f64", "f32", "f16"):
-            steps_f = max(10, args.steps // (8 if fprec == "f64" else 1))
-            fms, fkt, _, fst = time_form("nonorth_d3q15", fprec, args.edge, steps_f, args.warmup, world)
-            f_fused = fkt["fused_ms"] / max(fkt["fused_launches"], 1)
-            f_psi = fkt["psi_ms"] / max(fkt["psi_launches"], 1)
-            fb, pb = FUSED_BYTES_Q15[fprec], PSI_BYTES_Q15[fprec]
-            extra = {}
-            if fprec == "f64":
-                extra["fp64_alu_frac_fused"] = (FUSED_FP64_INSTR["nonorth_d3q15"] * n / (f_fused / 1e3) / 1e9
-                                                / FP64_PEAK_GINSTR)
-            forms[f"nonorth_d3q15_{fprec}_droplet"] = {**extra,
-                "mlups": n * steps_f / (fms / 1e3) / 1e6, "ms_per_step": fms / steps_f, "fused_ms": f_fused,
-                "psi_ms": f_psi, "fused_gbs": fb * n / (f_fused / 1e3) / 1e9,
-                "hbm_frac_fused": fb * n / (f_fused / 1e3) / 1e9 / hbm_peak,
-                "step_gbs": (fb + pb) * n / (fms / steps_f / 1e3) / 1e9, "bytes_per_lup_two_pass": fb + pb,
-                "status": fst, "note": "D3Q15 non-orthogonal variant (two-node kernels for FP32 arithmetic, one-node for FP64)"}
+            forms[f"nonorth_d3q15_{fprec}_droplet"] = form_entry("nonorth_d3q15", fprec, E, k64 if fprec == "f64" else K,
+                                                                 W, world, hbm_peak)
         for fprec in ("f32", "f16"):
-            fms, fkt, _, fst = time_form("nonorth", fprec, args.edge, args.steps, args.warmup, world,
-                                         eos_arith="f32x2")
-            f_fused = fkt["fused_ms"] / max(fkt["fused_launches"], 1)
-            f_psi = fkt["psi_ms"] / max(fkt["psi_launches"], 1)
-            forms[f"nonorth_{fprec}_droplet_eos_f32x2"] = {
-                "mlups": n * args.steps / (fms / 1e3) / 1e6, "ms_per_step": fms / args.steps, "fused_ms": f_fused,
-                "psi_ms": f_psi, "psi_gbs": PSI_BYTES[fprec] * n / (f_psi / 1e3) / 1e9, "status": fst,
-                "note": "EOS radicand in compensated FP32 pairs instead of FP64"}
+            forms[f"nonorth_{fprec}_droplet_eos_f32x2"] = form_entry("nonorth", fprec, E, K, W, world, hbm_peak,
+                                                                     eos_arith="f32x2")
         for fprec in ("f64", "f32"):
-            steps_f = max(10, args.steps // (8 if fprec == "f64" else 1))
-            fms, fkt, _, fst = time_form("nonorth", fprec, args.edge, steps_f, args.warmup, world, field="flat")
-            f_fused = fkt["fused_ms"] / max(fkt["fused_launches"], 1)
-            forms[f"nonorth_{fprec}_flat"] = {"mlups": n * steps_f / (fms / 1e3) / 1e6, "ms_per_step": fms / steps_f,
-                                             "fused_ms": f_fused,
-                                             "hbm_frac_fused": FUSED_BYTES[fprec] * n / (f_fused / 1e3) / 1e9 / hbm_peak,
-                                             "status": fst}
+            forms[f"nonorth_{fprec}_flat"] = form_entry("nonorth", fprec, E, k64 if fprec == "f64" else K, W, world,
+                                                        hbm_peak, field="flat")
 
     if args.forms in ("all", "batched"):
         forms[f"batched_{args.batch_boxes}"] = batched_run(args.steps, args.warmup, args.batch_boxes)
@@ -639,14 +812,20 @@ def main():
         "vs_baseline": None, "dtype": "f64" if prec == "f64" else "f32", "data": "synthetic",
         "config": {"workload": workload_text(op, prec, args.edge),
                    "edge": args.edge, "operator": op, "precision": prec,
+                   "step": "work-list single pass" if single == "queue" else (f"single pass ({single})" if single
+                                                                            else "two-pass"),
                    "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": f"inputs larger than L2 (populations {(15 if op == 'nonorth_d3q15' else 19) * n * {'f64': 8, 'f32': 4, 'f16': 2}[prec] / 1e9:.2f} GB per buffer)"},
+                   "l2": f"inputs larger than L2 (populations {(15 if q15 else 19) * n * {'f64': 8, 'f32': 4, 'f16': 2}[prec] / 1e9:.2f} GB per buffer)"},
+        "timing": f"median of {args.repeats} regions of {args.steps} steps (CUDA events on the launch stream, "
+                  f"barrier + synchronize around each); kernel split from a separate region",
+        "region_ms": r["region_ms"],
         "roofline": roofline,
-        "clocks": clocks,
+        "whole_step": whole,
+        "clocks": r["clocks"],
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": launches,
         "forms": forms,
-        "status": status,
+        "status": r["status"],
     }
     if cpu:
         out["cpu_baseline"] = cpu

@@ -178,8 +178,9 @@ lbm_status lbm_set_profiling(lbm_ctx *ctx, int enabled);
 lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
                             double *ms_fused, long long *n_fused);
 
-/* Kernel choice for this context.  single_pass = 0 (the default) runs the psi
- * pass and the fused pass.  1 (LBM_F32 and LBM_F32_STORE_F16 only) runs each
+/* Kernel choice for this context.  The default is 5 (below) for an LBM_F32
+ * D3Q19 context with an even Nx, the faster step there on GB300, and 0
+ * otherwise.  single_pass = 0 runs the psi pass and the fused pass.  1 (LBM_F32 and LBM_F32_STORE_F16 only) runs each
  * step as one kernel that also produces psi of the next step, recomputing
  * collisions on a one-node ring around each thread block's tile.  2 runs that
  * single pass with its data moved by bulk asynchronous copies (LBM_F32 only,

@@ -5,16 +5,18 @@
 // Work item k is a pair of tile jobs (64 x 4 nodes of one plane, one node
 // pair per thread):
 //   fused job (z, tile): the fused pass (Eqs. 4-6 and 15, pull streaming of
-//     Eq. 5): reads f(t) and psi(t), writes f*(t); each warp then counts its
-//     row done;
+//     Eq. 5): reads f(t) and psi(t), writes f*(t); then counts itself done;
 //   psi job (z', tile'): the psi pass of the next step: rho(t+1) from the
 //     pulled f*(t) (Eq. 6), the EOS, psi(t+1).  It needs the fused jobs of
 //     planes z'-1..z'+1 on the tile and its eight neighbours (periodic) and
 //     pulls their output through L2, where it still is.
 // The host builds the list (and checks it): fused jobs plane by plane; each
-// psi job in the first free item at least one wave of the grid (`grid` items)
-// after the last fused job it reads, so that by the time a block reaches it
-// those fused jobs were taken a round earlier and the wait is one poll.  Block b works through items b, b + grid, b + 2 grid, ...; the
+// psi job in the first free item at least half a wave of the grid (grid / 2
+// items) after the last fused job it reads.  Half a wave: by the time a block
+// reaches the psi job those fused jobs are normally finished, so the wait is
+// one poll, while writer and reader stay close enough for the populations to
+// be still in L2 (measured on GB300: a whole wave waits less but re-reads about
+// twice as much from DRAM, and is slower; a quarter waits more).  Block b works through items b, b + grid, b + 2 grid, ...; the
 // launch is cooperative (every block resident), so the unfinished item with
 // the lowest index always has its block at it and waits only on earlier fused
 // jobs, which are finished: progress needs no timing assumption.  Waits are
@@ -23,15 +25,14 @@
 //
 // What this buys over two launches: the psi jobs' FP64 EOS runs on the same
 // SMs while the fused jobs stream HBM, and the populations they pull come from
-// L2 (writer and reader are about two planes plus one wave of tiles apart): DRAM traffic per node is f(t) read and f*(t) written once plus psi
+// L2 (writer and reader are about two planes plus half a wave of tiles apart): DRAM traffic per node is f(t) read and f*(t) written once plus psi
 // read and written once (2 x 19 x s + 8 bytes) against 3 x 19 x s + 8.  The
 // arithmetic and its order are those of the two-pass kernels, so the results
 // are equal bit for bit.
 //
-// Counters: done[z * T + tile] counts the rows of fused job (z, tile) finished
-// over all launches (each of the kRows warps adds one after its stores), so a
-// psi job of launch `stamp` waits for done >= kRows * stamp and nothing is
-// ever reset.
+// Counters: done[z * T + tile] counts the launches in which fused job
+// (z, tile) has finished (one release increment after a block barrier), so a
+// psi job of launch `stamp` waits for done >= stamp and nothing is ever reset.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -78,8 +79,8 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
       asm volatile("" : "+r"(z), "+r"(t));  // keep the row offsets out of the registers across items
       const int x = (t % G.ntx) * 2 * TXP + 2 * lane, y = (t / G.ntx) * kRows + row;
       if (x < P.nx && y < P.ny) fused_pair_at<S, OP, SIGMA, false>(g_in, g_out, psi_in, P, x, y, z, Rates<V2>(P));
-      __syncwarp();
-      if (lane == 0) counter_release_add(done + z * G.T + t, 1);
+      __syncthreads();
+      if (lane == 0 && row == 0) counter_release_add(done + z * G.T + t, 1);
     }
     if (it.z >= 0) {
       int z = it.z, t = it.w;
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
         xx = xx < 0 ? xx + G.ntx : (xx >= G.ntx ? xx - G.ntx : xx);
         yy = yy < 0 ? yy + G.nty : (yy >= G.nty ? yy - G.nty : yy);
         const int *c = done + zz * G.T + yy * G.ntx + xx;
-        const int target = kRows * (stamp + P.wait_bias);
+        const int target = stamp + P.wait_bias;
         for (int n = 0; counter_acquire(c) < target; ++n) {
           if (n >= P.spin_limit) {
             ok = false;
@@ -191,10 +192,9 @@ bool queue_items(const KParams &P, int grid, std::vector<int4> &out) {
   const long long nf = (long long)P.nz * G.T;
   if (P.nz < 3 || grid < 1 || nf >= (1LL << 30)) return false;
   // fused job j = (j / T, j % T); psi job (z, t) is ready after the last of the
-  // 27 fused jobs it reads and goes to the first free item >= ready + lag: one
-  // wave of the grid later, so its block reaches it a round after the last of
-  // those fused jobs was taken
-  const long long lag = grid;
+  // 27 fused jobs it reads and goes to the first free item >= ready + lag, half
+  // a wave of the grid later (at least one item)
+  const long long lag = std::max(1, grid / 2);
   std::vector<long long> ready((size_t)nf);
   for (long long p = 0; p < nf; ++p) {
     const int z = (int)(p / G.T), t = (int)(p % G.T), tx = t % G.ntx, ty = t / G.ntx;

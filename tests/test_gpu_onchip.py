@@ -33,8 +33,7 @@ def _run(grid, op, prec, steps, mode, eos_arith="f64", sigma=0.0, R=8.0):
     phys = physics(T_over_Tc=0.8, sigma=sigma)
     rl, rv = coexistence(0.8)
     lat = lattice(grid, op, prec, phys)
-    if mode:
-        lat.set_tuning(mode, 1, 0)
+    lat.set_tuning(mode, 1, 0)  # False: the two-pass step, explicitly (FP32 storage defaults to the work list)
     lat.set_eos_arith(eos_arith)
     lat.init_droplet(tuple(n / 2 for n in grid), R, 2.0, rl, rv)
     d0 = lat.diag()

@@ -32,8 +32,7 @@ def _built():
 def _run(grid, op, prec, mode, steps, sigma=0.0, eos_arith="f64", rates=None, T=0.8, R=None):
     phys = physics(T_over_Tc=T, sigma=sigma, rates=rates)
     lat = lattice(grid, op, prec, phys)
-    if mode:
-        lat.set_tuning(mode, 1, 0)
+    lat.set_tuning(mode, 1, 0)  # False: the two-pass step, explicitly (FP32 storage defaults to the work list)
     if eos_arith != "f64":
         lat.set_eos_arith(eos_arith)
     rl, rv = coexistence(T)
@@ -82,8 +81,7 @@ def test_queue_exponential_pseudopotential():
     outs = []
     for mode in (False, "queue"):
         lat = lattice(grid, "nonorth", "f32", phys)
-        if mode:
-            lat.set_tuning(mode, 1, 0)
+        lat.set_tuning(mode, 1, 0)  # False: the two-pass step, explicitly (FP32 storage defaults to the work list)
         lat.init_field(rho0, rho_ref=rv)
         lat.step(30)
         assert lat.check() == 0
@@ -150,8 +148,7 @@ def test_queue_at_256_cubed_equals_two_pass():
     for mode in (False, "queue"):
         lat = Lattice((edge,) * 3, operator="nonorth", precision="f32", T=0.7 * Tc, G=-1.0,
                       rates=Rates(s_e=1.1, s_nu=1.0, s_q=1.1, s_pi=1.1, s_eps=1.1, s_m=1.1), sigma=0.105)
-        if mode:
-            lat.set_tuning(mode, 1, 0)
+        lat.set_tuning(mode, 1, 0)  # False: the two-pass step, explicitly (FP32 storage defaults to the work list)
         lat.init_droplet((edge / 2,) * 3, 40.0, 3.0, rl, rv)
         lat.step(steps)
         assert lat.check() == 0
@@ -160,3 +157,15 @@ def test_queue_at_256_cubed_equals_two_pass():
         torch.cuda.empty_cache()
     (r0, u0), (r1, u1) = outs
     assert np.array_equal(r0, r1) and np.array_equal(u0, u1)
+
+
+def test_default_step_per_form():
+    """FP32 storage on D3Q19 with an even Nx steps on the work list by default; FP16 storage, FP64, an odd
+    Nx and D3Q15 keep the two-pass step."""
+    cases = [((16, 16, 16), "nonorth", "f32", "queue"), ((16, 16, 16), "orth", "f32", "queue"),
+             ((16, 16, 16), "nonorth", "f16", False), ((16, 16, 16), "nonorth", "f64", False),
+             ((15, 16, 16), "nonorth", "f32", False), ((16, 16, 16), "nonorth_d3q15", "f32", False)]
+    for grid, op, prec, want in cases:
+        lat = lattice(grid, op, prec, physics())
+        assert lat.tuning()["single_pass"] == want, (grid, op, prec)
+        lat.close()
