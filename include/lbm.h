@@ -307,8 +307,16 @@ lbm_status lbm_batch_init_droplet(lbm_batch *b, int id, const double centre[3], 
 lbm_status lbm_batch_init_flat(lbm_batch *b, int id, int axis, double lo, double hi, double W, double rho_l,
                                double rho_v);
 
-/* Tile shape of the batch (0: 32x4, 1: 32x8, 2: 64x4) and, for box id >= 0, its
- * z planes per work item (0 = automatic).  Results do not depend on either. */
+/* Step of the batch: 3 (the default) the work-list single pass when every box
+ * has an even Nx (one cooperative launch per step over 64x4 tile jobs of all
+ * boxes: fused jobs and the next step's psi jobs, each box's psi jobs half a
+ * wave of the grid behind the fused jobs they read; its completion counters,
+ * 4 bytes per tile and plane, are cleared by a memset in the step graph); 0, 1,
+ * 2 the tile shape (32x4, 32x8, 64x4) of the two-pass pair kernels, or of the
+ * one-node single pass that any batch with an odd-Nx box runs; and, for box id
+ * >= 0, its z planes per work item of those (0 = automatic).  Results do not
+ * depend on the choice (the work list and the two-pass kernels are equal bit
+ * for bit). */
 lbm_status lbm_batch_set_tuning(lbm_batch *b, int tile, int id, int z_planes);
 
 /* Advance every initialised box n >= 1 steps (even n replays the two-step graph

@@ -28,6 +28,9 @@ bool fill_params(const int grid[3], const lbm_eos *eos, double G, const lbm_rate
 
 namespace {
 
+// lbm_batch_set_tuning's tile value for the work-list single pass (64x4 tile jobs)
+constexpr int kTileWorkList = 3;
+
 struct HostBox {
   bool live = false;
   BatchBox d{};        // descriptor as the kernel sees it
@@ -46,8 +49,8 @@ struct lbm_batch {
   int precision = 1, eos = 0;
   cudaStream_t stream = nullptr;
   size_t budget = 0, used = 0;
-  int tile = lbm::kTile32x8;
-  int grid_blocks = 0;       // persistent grid size
+  int tile = kTileWorkList;  // step kind: the work list, or the tile shape of the other kernels
+  int grid_blocks = 0;       // SMs (persistent grid sizes are multiples of it)
   std::vector<HostBox> boxes;
   BatchBox *d_boxes = nullptr;
   int4 *d_items = nullptr;
@@ -59,6 +62,10 @@ struct lbm_batch {
   int cap_red = 0;
   bool dirty = true;         // descriptors / items need uploading, graphs re-capturing
   bool pair = false;         // the captured step is the two-pass pair kernels
+  bool wl = false;           // ... or the work-list single pass
+  int *d_done = nullptr;     // its completion counters, cleared before every launch
+  long long cap_done = 0, ndone = 0;
+  int wl_grid = 0;
   // graphs of two steps and of one step, for each starting parity: the state of
   // box h is at level h.d.cur ^ phase, and a step at parity `phase` moves it to
   // the other level, so an odd step count flips phase instead of the descriptors
@@ -120,16 +127,61 @@ lbm_status rebuild(lbm_batch *b) {
     if (b->boxes[i].live && b->boxes[i].initialised) order.push_back({(long long)b->boxes[i].d.P.n, i});
   }
   std::sort(order.begin(), order.end(), [](auto &x, auto &y) { return x.first > y.first || (x.first == y.first && x.second < y.second); });
-  int bx, by;
-  lbm::onepass_tile_shape(b->tile, &bx, &by);
+  bool pair = true;
+  for (auto &o : order) pair = pair && b->boxes[o.second].d.P.nx % 2 == 0;
+  const bool wl = pair && b->tile == kTileWorkList;
   std::vector<int4> items;
-  for (auto &o : order) {
-    const HostBox &h = b->boxes[o.second];
-    const KParams &P = h.d.P;
-    const int tx = (P.nx + bx - 1) / bx, ty = (P.ny + by - 1) / by, zc = h.zc > 0 ? h.zc : default_zc(P);
-    for (int z0 = 0; z0 < P.nz; z0 += zc)
-      for (int j = 0; j < ty; ++j)
-        for (int i = 0; i < tx; ++i) items.push_back(make_int4(o.second, i | (j << 16), z0, std::min(z0 + zc, P.nz)));
+  if (wl) {
+    // the work list over the boxes in this order; each box's counters start at its qbase
+    BCK(lbm::batch_queue_grid(b->precision, b->eos, &b->wl_grid), "work list occupancy");
+    std::vector<const KParams *> ps;
+    for (auto &o : order) ps.push_back(&b->boxes[o.second].d.P);
+    std::vector<int> base;
+    long long nc = 0;
+    if (!lbm::batch_queue_items(ps, b->wl_grid, items, base, &nc)) return bfail(b, LBM_ERR_ARG, "no valid work list");
+    for (size_t k = 0; k < order.size(); ++k) {
+      BatchBox &d = b->boxes[order[k].second].d;
+      d.qbase = base[k];
+      d.tw = lbm::batch_tile_width(d.P.nx);
+      desc[order[k].second].qbase = d.qbase;
+      desc[order[k].second].tw = d.tw;
+    }
+    // the list numbers boxes in `order`; the kernel reads the descriptor table by slot: renumber, then
+    // check every job against the descriptor it will read (plane and tile inside that box, counter
+    // inside the counter array)
+    for (auto &it : items) {
+      if (it.x >= 0) it.x = order[it.x].second;
+      if (it.z >= 0) it.z = order[it.z].second;
+      for (int side = 0; side < 2; ++side) {
+        const int slot = side ? it.z : it.x;
+        if (slot < 0) continue;
+        const KParams &P = desc[slot].P;
+        const unsigned zt = (unsigned)(side ? it.w : it.y);
+        const long long z = zt & 0xffffu, t = zt >> 16;
+        const long long T = lbm::batch_queue_tiles(P);
+        if (slot >= nb || !b->boxes[slot].live || z >= P.nz || t >= T || desc[slot].qbase + P.nz * T > nc)
+          return bfail(b, LBM_ERR_ARG, "work list does not match the box table");
+      }
+    }
+    if (nc > b->cap_done) {
+      if (b->d_done) cudaFreeAsync(b->d_done, b->stream);
+      b->d_done = nullptr;
+      BCK(cudaMallocAsync((void **)&b->d_done, sizeof(int) * std::max(nc, 1LL), b->stream), "work list counters");
+      b->cap_done = nc;
+    }
+    b->ndone = nc;
+  } else {
+    int bx, by;
+    lbm::onepass_tile_shape(b->tile == kTileWorkList ? lbm::kTile32x8 : b->tile, &bx, &by);
+    for (auto &o : order) {
+      const HostBox &h = b->boxes[o.second];
+      const KParams &P = h.d.P;
+      const int tx = (P.nx + bx - 1) / bx, ty = (P.ny + by - 1) / by, zc = h.zc > 0 ? h.zc : default_zc(P);
+      for (int z0 = 0; z0 < P.nz; z0 += zc)
+        for (int j = 0; j < ty; ++j)
+          for (int i = 0; i < tx; ++i)
+            items.push_back(make_int4(o.second, i | (j << 16), z0, std::min(z0 + zc, P.nz)));
+    }
   }
   if ((int)items.size() > b->cap_items) {
     if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
@@ -142,21 +194,27 @@ lbm_status rebuild(lbm_batch *b) {
     BCK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, b->stream), "H2D items");
   BCK(cudaStreamSynchronize(b->stream), "sync");  // host vectors go out of scope
   destroy_graphs(b);
-  bool pair = true;
-  for (auto &o : order) pair = pair && b->boxes[o.second].d.P.nx % 2 == 0;
-  b->pair = pair;
+  b->pair = pair && !wl;
+  b->wl = wl;
   if (b->nitems) {
     // resident blocks per SM: the pair kernels' own occupancy (the psi kernel needs half the fused kernel's
     // registers), the single-pass kernel's launch bounds
+    const int tile = b->tile == kTileWorkList ? lbm::kTile32x8 : b->tile;
     int pair_per_sm[2] = {1, 1};
-    if (pair) BCK(lbm::batch_pair_occupancy(b->precision, b->eos, b->tile, pair_per_sm), "pair kernel occupancy");
-    const int per_sm = b->tile == lbm::kTile32x4 ? 4 : 2;
+    if (b->pair) BCK(lbm::batch_pair_occupancy(b->precision, b->eos, tile, pair_per_sm), "pair kernel occupancy");
+    const int per_sm = tile == lbm::kTile32x4 ? 4 : 2;
     const int grid = std::min(b->grid_blocks * per_sm, b->nitems);
     auto step = [&](int parity) {
-      return pair ? lbm::launch_batch_pair(b->precision, b->eos, b->tile, b->d_boxes, b->d_items, b->nitems, parity,
-                                           b->grid_blocks, pair_per_sm, b->d_err, b->stream)
-                  : lbm::launch_batch_onepass(b->precision, b->eos, b->tile, b->d_boxes, b->d_items, b->nitems,
-                                              parity, grid, b->d_err, b->stream);
+      if (wl) {
+        cudaError_t e = cudaMemsetAsync(b->d_done, 0, sizeof(int) * (size_t)b->ndone, b->stream);
+        if (e != cudaSuccess) return e;
+        return lbm::launch_batch_queue(b->precision, b->eos, b->d_boxes, b->d_items, b->nitems, parity, b->wl_grid,
+                                       b->d_done, b->d_err, b->stream);
+      }
+      return b->pair ? lbm::launch_batch_pair(b->precision, b->eos, tile, b->d_boxes, b->d_items, b->nitems, parity,
+                                              b->grid_blocks, pair_per_sm, b->d_err, b->stream)
+                     : lbm::launch_batch_onepass(b->precision, b->eos, tile, b->d_boxes, b->d_items, b->nitems,
+                                                 parity, grid, b->d_err, b->stream);
     };
     for (int k = 0; k < 4; ++k) {  // g2[0], g2[1], g1[0], g1[1]
       const int two = k < 2, p0 = k & 1;
@@ -339,7 +397,7 @@ lbm_status lbm_batch_init_flat(lbm_batch *b, int id, int axis, double lo, double
 }
 
 lbm_status lbm_batch_set_tuning(lbm_batch *b, int tile, int id, int z_planes) {
-  if (!b || tile < 0 || tile > 2 || z_planes < 0) return bfail(b, LBM_ERR_ARG, "bad tuning");
+  if (!b || tile < 0 || tile > kTileWorkList || z_planes < 0) return bfail(b, LBM_ERR_ARG, "bad tuning");
   b->tile = tile;
   if (id >= 0) {
     HostBox *h = get_box(b, id);
@@ -422,6 +480,7 @@ lbm_status lbm_batch_check(lbm_batch *b) {
   BCK(cudaMemcpyAsync(&w, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream), "read error word");
   BCK(cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream), "clear error word");
   BCK(cudaStreamSynchronize(b->stream), "sync");
+  if (w & lbm::kErrTimeout) return bfail(b, LBM_ERR_TIMEOUT, "a bounded wait of the work-list step gave up");
   if (w & lbm::kErrNonFinite) return bfail(b, LBM_ERR_NONFINITE, "non-finite density");
   if (w & lbm::kErrEosDomain) return bfail(b, LBM_ERR_EOS_DOMAIN, "density left the domain of the EOS");
   return LBM_OK;
@@ -455,6 +514,7 @@ void lbm_batch_destroy(lbm_batch *b) {
   if (b->d_boxes) cudaFreeAsync(b->d_boxes, b->stream);
   if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
   if (b->d_red) cudaFreeAsync(b->d_red, b->stream);
+  if (b->d_done) cudaFreeAsync(b->d_done, b->stream);
   if (b->d_err) cudaFreeAsync(b->d_err, b->stream);
   if (b->d_scratch) cudaFreeAsync(b->d_scratch, b->stream);
   cudaStreamSynchronize(b->stream);

@@ -135,7 +135,8 @@ struct BatchBox {
   float *psi[2];
   int op;
   int cur;
-  int pad[2];
+  int qbase;  // first completion counter of this box in the batch work list
+  int tw;     // its tile width there (batch_tile_width)
 };
 
 // Persistent single-pass launch over the work items (box, tx | ty << 16, z0, z1)
@@ -202,6 +203,20 @@ bool queue_items(const KParams &P, int grid, std::vector<int4> &out);
 cudaError_t launch_queue(const KParams &P, int precision, int op, bool sigma, bool df, const void *g_in, void *g_out,
                          const void *psi_in, void *psi_out, const QueueState &q, int stamp, unsigned *err,
                          cudaStream_t s);
+
+// The work-list step over a batch (every box D3Q19 with an even Nx): one
+// cooperative launch per step; items hold a fused tile job and a psi tile job
+// of any boxes (x / z: box index or -1, y / w: z | tile << 16).  The list is
+// built for the boxes in the given order; base[k] receives box k's first
+// completion counter, *ncounters their total.  Counters must be zero when a
+// launch starts (the step graph clears them).
+bool batch_queue_items(const std::vector<const KParams *> &boxes, int grid, std::vector<int4> &out,
+                       std::vector<int> &base, long long *ncounters);
+int batch_tile_width(int nx);               // 64, 32 or 16: tiles of tw x (256 / tw) nodes
+int batch_queue_tiles(const KParams &P);   // tile jobs per plane of a box in a batch work list
+cudaError_t batch_queue_grid(int precision, int eos, int *grid);
+cudaError_t launch_batch_queue(int precision, int eos, const BatchBox *boxes, const int4 *items, int nitems,
+                               int parity, int grid, int *done, unsigned *err, cudaStream_t s);
 
 size_t storage_bytes(int precision);  // bytes per stored population
 size_t psi_elem_bytes(int precision);

@@ -170,6 +170,127 @@ cudaError_t occupancy_of(int *per_sm) {
   return cudaSuccess;
 }
 
+// ------------------------------------------------------------------ batches
+// The same work list over many boxes.  Every job carries its box, whose
+// descriptor (parameters, buffers, operator, level, tile width) the threads
+// read from global memory through the read-only path; a fused job of box B
+// reads level in = B.cur ^ parity and writes in ^ 1, the psi job evaluates psi
+// of level in ^ 1.  Both operators and the Eq. 16 term (zero coefficient when
+// off) are compiled in.  Tiles are tw x (256 / tw) nodes, tw = 64, 32 or 16 per
+// box (batch_tile_width): 128 threads, one node pair each, and on the small
+// boxes of a batch (edges 32, 48, 96, ...) no idle half tiles.
+struct BatchGeo {
+  int tw, th, ntx, nty, T;  // tile width and height, tiles along x and y, per plane
+};
+
+__host__ __device__ inline BatchGeo batch_geo(const KParams &P, int tw) {
+  BatchGeo g;
+  g.tw = tw;
+  g.th = 2 * NTH / tw;
+  g.ntx = (P.nx + tw - 1) / tw;
+  g.nty = (P.ny + g.th - 1) / g.th;
+  g.T = g.ntx * g.nty;
+  return g;
+}
+
+template <typename S, int EOS>
+__global__ void __launch_bounds__(NTH, kMinBlocks)
+    batch_queue_kernel(const BatchBox *__restrict__ boxes, const int4 *__restrict__ items, int nitems, int parity,
+                       int *__restrict__ done, unsigned *__restrict__ err) {
+  const int tid = threadIdx.y * TXP + threadIdx.x;
+  unsigned e = 0;
+#pragma unroll 1
+  for (int k = blockIdx.x; k < nitems; k += gridDim.x) {
+    const int4 it = __ldg(items + k);
+    if (it.x >= 0) {
+      const BatchBox &B = boxes[it.x];
+      const KParams &P = B.P;
+      const BatchGeo G = batch_geo(P, B.tw);
+      int z = (int)((unsigned)it.y & 0xffffu), t = (int)((unsigned)it.y >> 16);
+      asm volatile("" : "+r"(z), "+r"(t));
+      const int in = B.cur ^ parity, half = G.tw / 2;
+      const int x = (t % G.ntx) * G.tw + 2 * (tid % half), y = (t / G.ntx) * G.th + tid / half;
+      if (x < P.nx && y < P.ny) {
+        const S *gi = (const S *)B.g[in];
+        S *go = (S *)B.g[in ^ 1];
+        if (B.op == kNonOrth)
+          fused_pair_at<S, kNonOrth, true, false>(gi, go, B.psi[in], P, x, y, z, Rates<V2>(P));
+        else
+          fused_pair_at<S, kOrth, true, false>(gi, go, B.psi[in], P, x, y, z, Rates<V2>(P));
+      }
+      __syncthreads();
+      if (tid == 0) counter_release_add(done + B.qbase + z * G.T + t, 1);
+    }
+    if (it.z >= 0) {
+      const BatchBox &B = boxes[it.z];
+      const KParams &P = B.P;
+      const BatchGeo G = batch_geo(P, B.tw);
+      int z = (int)((unsigned)it.w & 0xffffu), t = (int)((unsigned)it.w >> 16);
+      asm volatile("" : "+r"(z), "+r"(t));
+      const int tx = t % G.ntx, ty = t / G.ntx, lane = threadIdx.x;
+      bool ok = true;
+      if (lane < 27) {  // fused jobs of planes z-1..z+1 on the 3 x 3 tiles around (tx, ty)
+        int zz = z + lane / 9 - 1, xx = tx + lane % 3 - 1, yy = ty + (lane / 3) % 3 - 1;
+        zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
+        xx = xx < 0 ? xx + G.ntx : (xx >= G.ntx ? xx - G.ntx : xx);
+        yy = yy < 0 ? yy + G.nty : (yy >= G.nty ? yy - G.nty : yy);
+        const int *c = done + B.qbase + zz * G.T + yy * G.ntx + xx;
+        const int target = 1 + P.wait_bias;  // counters are cleared before every launch
+        for (int n = 0; counter_acquire(c) < target; ++n) {
+          if (n >= P.spin_limit) {
+            ok = false;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      if (!__all_sync(0xffffffffu, ok)) e |= kErrTimeout;
+      const int in = B.cur ^ parity, half = G.tw / 2;
+      const int x = tx * G.tw + 2 * (tid % half), y = ty * G.th + tid / half;
+      if (x < P.nx && y < P.ny) psi_pair_at_l2<S, EOS, false>((const S *)B.g[in ^ 1], B.psi[in ^ 1], P, x, y, z, e);
+    }
+  }
+  if (e) atomicOr(err, e);
+}
+
+template <typename S, int EOS>
+cudaError_t batch_launch(const BatchBox *boxes, const int4 *items, int nitems, int parity, int grid, int *done,
+                         unsigned *err, cudaStream_t s, int *per_sm) {
+  auto kern = batch_queue_kernel<S, EOS>;
+  if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, NTH, 0);
+  void *args[] = {(void *)&boxes, (void *)&items, (void *)&nitems, (void *)&parity, (void *)&done, (void *)&err};
+  return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(TXP, kRows), args, 0, s);
+}
+
+template <typename S>
+cudaError_t batch_by_eos(int eos, const BatchBox *boxes, const int4 *items, int nitems, int parity, int grid,
+                         int *done, unsigned *err, cudaStream_t s, int *per_sm) {
+  switch (eos) {
+    case kEosCS: return batch_launch<S, kEosCS>(boxes, items, nitems, parity, grid, done, err, s, per_sm);
+    case kEosExp: return batch_launch<S, kEosExp>(boxes, items, nitems, parity, grid, done, err, s, per_sm);
+    default: return batch_launch<S, kEosNone>(boxes, items, nitems, parity, grid, done, err, s, per_sm);
+  }
+}
+
+// Psi jobs go to the first free item at least `lag` items after the last of
+// the fused jobs they read (ready[]); fused job j sits in item j.  Checks the
+// result as the single-box list does.
+bool place_psi_jobs(std::vector<int4> &out, const std::vector<long long> &ready, const std::vector<int2> &job,
+                    long long nf, long long lag) {
+  std::vector<long long> order((size_t)nf);
+  for (long long p = 0; p < nf; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(), [&](long long a, long long b) { return ready[a] < ready[b]; });
+  long long next = 0;
+  for (long long p : order) {
+    const long long k = std::max(next, ready[p] + lag);
+    while ((long long)out.size() <= k) out.push_back(make_int4(-1, -1, -1, -1));
+    out[k].z = job[p].x;
+    out[k].w = job[p].y;
+    next = k + 1;
+  }
+  return (long long)out.size() < (1LL << 31);
+}
+
 }  // namespace
 
 bool queue_supported(const KParams &P, int precision) { return precision != kF64 && P.nx % 2 == 0 && P.q == 19; }
@@ -248,6 +369,104 @@ cudaError_t launch_queue(const KParams &P, int precision, int op, bool sigma, bo
   if (!queue_supported(P, precision)) return cudaErrorInvalidValue;
   if (precision == kF32) return by_op<float>(P, op, sigma, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
   return by_op<__half>(P, op, sigma, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
+}
+
+int batch_tile_width(int nx) {
+  // the widest of 64, 32, 16 with the fewest idle columns in the last tile
+  int best = 64;
+  long long waste = (long long)(nx + 63) / 64 * 64 - nx;
+  for (int tw : {32, 16}) {
+    const long long w = (long long)(nx + tw - 1) / tw * tw - nx;
+    if (w < waste) best = tw, waste = w;
+  }
+  return best;
+}
+
+int batch_queue_tiles(const KParams &P) { return batch_geo(P, batch_tile_width(P.nx)).T; }
+
+bool batch_queue_items(const std::vector<const KParams *> &boxes, int grid, std::vector<int4> &out,
+                       std::vector<int> &base, long long *ncounters) {
+  // fused jobs box by box, plane by plane: global fused position = item index
+  std::vector<long long> first(boxes.size() + 1, 0);
+  base.assign(boxes.size(), 0);
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    const KParams &P = *boxes[b];
+    const BatchGeo G = batch_geo(P, batch_tile_width(P.nx));
+    if (P.nz < 3 || P.nx % 2 != 0 || P.nz > 0xffff || G.T > 0xffff || grid < 1) return false;
+    first[b + 1] = first[b] + (long long)P.nz * G.T;
+    if (first[b + 1] >= (1LL << 30)) return false;
+    base[b] = (int)first[b];
+  }
+  const long long nf = first.back();
+  *ncounters = nf;
+  out.assign((size_t)nf, make_int4(-1, -1, -1, -1));
+  std::vector<long long> ready((size_t)nf);
+  std::vector<int2> job((size_t)nf);  // (box, z | tile << 16) of psi job p (same numbering as fused job p)
+  for (size_t b = 0; b < boxes.size(); ++b) {
+    const KParams &P = *boxes[b];
+    const BatchGeo G = batch_geo(P, batch_tile_width(P.nx));
+    for (int z = 0; z < P.nz; ++z)
+      for (int t = 0; t < G.T; ++t) {
+        const long long j = first[b] + (long long)z * G.T + t;
+        const int zt = (int)((unsigned)z | ((unsigned)t << 16));
+        out[j] = make_int4((int)b, zt, -1, -1);
+        job[j] = make_int2((int)b, zt);
+        const int tx = t % G.ntx, ty = t / G.ntx;
+        long long r = -1;
+        for (int dz = -1; dz <= 1; ++dz)
+          for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+              const int zz = (z + dz + P.nz) % P.nz, yy = (ty + dy + G.nty) % G.nty, xx = (tx + dx + G.ntx) % G.ntx;
+              r = std::max(r, first[b] + (long long)zz * G.T + yy * G.ntx + xx);
+            }
+        ready[j] = r;
+      }
+  }
+  if (!place_psi_jobs(out, ready, job, nf, std::max(1, grid / 2))) return false;
+  // check: every job once, each psi job in an item after the fused jobs it reads
+  std::vector<char> fseen((size_t)nf, 0), pseen((size_t)nf, 0);
+  for (size_t k = 0; k < out.size(); ++k) {
+    const int4 it = out[k];
+    for (int side = 0; side < 2; ++side) {
+      const int b = side ? it.z : it.x;
+      if (b < 0) continue;
+      if (b >= (int)boxes.size()) return false;
+      const unsigned zt = (unsigned)(side ? it.w : it.y);
+      const int z = (int)(zt & 0xffffu), t = (int)(zt >> 16);
+      const BatchGeo G = batch_geo(*boxes[b], batch_tile_width(boxes[b]->nx));
+      if (z >= boxes[b]->nz || t >= G.T) return false;
+      const long long j = first[b] + (long long)z * G.T + t;
+      if (!side) {
+        if (j != (long long)k || fseen[j]) return false;
+        fseen[j] = 1;
+      } else {
+        if (pseen[j] || ready[j] >= (long long)k) return false;
+        pseen[j] = 1;
+      }
+    }
+  }
+  for (long long p = 0; p < nf; ++p)
+    if (!fseen[p] || !pseen[p]) return false;
+  return true;
+}
+
+cudaError_t batch_queue_grid(int precision, int eos, int *grid) {
+  int per_sm = 0, dev = 0, sms = 0;
+  cudaError_t e = precision == kF32 ? batch_by_eos<float>(eos, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, 0, &per_sm)
+                                    : batch_by_eos<__half>(eos, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, 0, &per_sm);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  *grid = per_sm * sms;
+  return cudaSuccess;
+}
+
+cudaError_t launch_batch_queue(int precision, int eos, const BatchBox *boxes, const int4 *items, int nitems,
+                               int parity, int grid, int *done, unsigned *err, cudaStream_t s) {
+  if (precision == kF32) return batch_by_eos<float>(eos, boxes, items, nitems, parity, grid, done, err, s, nullptr);
+  if (precision == kF16) return batch_by_eos<__half>(eos, boxes, items, nitems, parity, grid, done, err, s, nullptr);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace lbm

@@ -1,4 +1,4 @@
-"""Autotuner for the single-pass kernel's tile shape and z planes per work item.
+"""Autotuner of the batched step (work list or tile shape, z planes per work item) and of a single box's step.
 
 Times a few steps of each candidate with CUDA events on the working stream and
 keeps the fastest.  Results do not depend on the choice (tested), so tuning can
@@ -7,7 +7,8 @@ run on the live state: every candidate step is a real step of the simulation.
 
 from __future__ import annotations
 
-TILES = {0: "32x4", 1: "32x8", 2: "64x4"}
+TILES = {0: "32x4", 1: "32x8", 2: "64x4", 3: "work list (64x4 tile jobs)"}
+WORK_LIST = 3
 
 
 def _time(step, n, stream):
@@ -22,13 +23,14 @@ def _time(step, n, stream):
     return e0.elapsed_time(e1) / n
 
 
-def tune_batch(batch, tiles=(0, 1, 2), z_planes=(16, 32, 64), steps=4):
-    """Pick the batch's tile and a common z-planes value; returns (tile, z, {candidate: ms/step})."""
+def tune_batch(batch, tiles=(WORK_LIST, 0, 1, 2), z_planes=(16, 32, 64), steps=4):
+    """Pick the batch's step kind (the work list, or a tile shape of the two-pass / single-pass kernels) and,
+    for the latter, a common z-planes value; returns (tile, z, {candidate: ms/step})."""
     stream = batch.stream
     boxes = list(batch.grids)
     results = {}
     for t in tiles:
-        for z in z_planes:
+        for z in ((0,) if t == WORK_LIST else z_planes):
             for b in boxes:
                 batch.set_tuning(t, b, z)
             batch.step(2)  # rebuild and warm the graph

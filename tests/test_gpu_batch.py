@@ -189,3 +189,64 @@ def test_odd_step_counts_neither_rebuild_nor_change_the_result():
     assert t0 == t1 == 2
     for (a_rho, a_u), (b_rho, b_u) in zip(r0, r1):
         assert np.array_equal(a_rho, b_rho) and np.array_equal(a_u, b_u)
+
+
+def _single_two_pass(spec, steps, prec):
+    grid, op, t, sigma, W = spec
+    lat = lattice(grid, op, prec, physics(T_over_Tc=t, sigma=sigma))
+    lat.set_tuning(False)
+    rl, rv = coexistence(t)
+    lat.init_droplet(tuple(n / 2 for n in grid), min(grid) / 4, W, rl, rv)
+    lat.step(steps)
+    out = lat.moments()
+    lat.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_work_list_batch_equals_two_pass_batch(prec):
+    """The batch's default step (the work list over all boxes, one launch per step) against the two-pass
+    pair kernels over an odd and an even number of steps: equal bit for bit in FP32.  With FP16 storage
+    the two-pass batch kernel can differ from single-box runs by one half-precision ulp (see above); the
+    work list equals the single-box two-pass step bit for bit there."""
+    outs = []
+    for tile in (3, 1):
+        b = _batch(prec)
+        ids = [_add(b, s, prec) for s in BOXES]
+        b.set_tuning(tile)
+        b.step(7)
+        b.step(6)
+        assert b.check() == 0
+        outs.append([b.moments(i) for i in ids])
+        b.close()
+    for spec, (r0, u0), (r1, u1) in zip(BOXES, *outs):
+        if prec == "f32":
+            assert np.array_equal(r0, r1) and np.array_equal(u0, u1), spec
+        else:
+            assert max_abs(r0, r1) <= 2e-3 and max_abs(u0, u1) <= 2e-3, spec
+            rs, us = _single_two_pass(spec, 13, prec)
+            assert np.array_equal(r0, rs) and np.array_equal(u0, us), spec
+
+
+def test_work_list_batch_against_the_oracle_and_join_leave():
+    """A box that joins a running work-list batch while another leaves evolves as the FP64 oracle says
+    (FP32 tolerance), and the descriptors' counter bases follow the rebuilt list."""
+    grid, op, t, sigma, W = BOXES[1]
+    phys = physics(T_over_Tc=t, sigma=sigma)
+    rl, rv = coexistence(t)
+    b = _batch()
+    p = _add(b, BOXES[0])
+    b.step(5)
+    q = _add(b, BOXES[1])
+    b.step(3)
+    b.remove(p)
+    _add(b, BOXES[3])
+    b.step(9)
+    assert b.check() == 0
+    rho, u = b.moments(q)
+    b.close()
+    po = oracle_params(grid, op, phys)
+    centre = tuple(n / 2 for n in grid)
+    f0 = L.equilibrium_state(po, droplet_rho(grid, centre, min(grid) / 4, W, rl, rv))
+    rho_o, u_o, _, _ = L.macroscopic(po, L.run(po, f0, 12))
+    assert max_abs(rho, rho_o) <= 2e-5 and max_abs(u, u_o) <= 2e-5
