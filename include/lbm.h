@@ -53,7 +53,9 @@ typedef enum {
   LBM_ERR_NONFINITE = 4,  /* a density or velocity became NaN or infinite         */
   LBM_ERR_EOS_DOMAIN = 5, /* rho <= 0, b rho/4 >= 1 or a negative sqrt radicand   */
   LBM_ERR_TIMEOUT = 6,    /* a bounded device-side wait gave up                   */
-  LBM_ERR_STATE = 7       /* call out of order (e.g. lbm_step before an init)     */
+  LBM_ERR_STATE = 7,      /* call out of order (e.g. lbm_step before an init)     */
+  LBM_ERR_BOUNDS = 8      /* debug build only: a kernel index fell outside its   */
+                          /* buffer (the access went to element 0 instead)       */
 } lbm_status;
 
 /* Transformation matrix: the usual orthogonal one, or Eq. 12 (Sec. II B), both
@@ -164,7 +166,9 @@ lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f, int on_device);
 lbm_status lbm_diag(lbm_ctx *ctx, double out[5]);
 
 /* Read and clear the device error word set by the kernels (synchronises):
- * LBM_OK, LBM_ERR_EOS_DOMAIN or LBM_ERR_NONFINITE. */
+ * LBM_OK, LBM_ERR_EOS_DOMAIN, LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT (a bounded
+ * wait of a single-pass kernel gave up) or, in the debug build of the library
+ * (compiled with LBM_BOUNDS_CHECK), LBM_ERR_BOUNDS. */
 lbm_status lbm_check(lbm_ctx *ctx);
 
 /* Make lbm_step run lbm_check every k steps (0, the default, never). */

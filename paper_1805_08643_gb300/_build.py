@@ -1,8 +1,11 @@
 """Build the in-tree CUDA library liblbm.so for sm_103a with nvcc.
 
-The two translation units compile in parallel; the link step produces
+The translation units compile in parallel; the link step produces
 ``paper_1805_08643_gb300/liblbm.so``.  A rebuild happens only when a source or
-header is newer than the library.
+header is newer than the library.  ``build(debug=True)`` makes the debug
+library ``liblbm_debug.so`` instead: the same sources compiled with
+LBM_BOUNDS_CHECK (kernel indices checked; lbm_check reports LBM_ERR_BOUNDS),
+loaded by the binding when LBM_DEBUG_LIBRARY=1 is set in the environment.
 """
 
 from __future__ import annotations
@@ -18,6 +21,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "liblbm.so")
+LIB_DEBUG = os.path.join(HERE, "liblbm_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
@@ -38,22 +42,27 @@ def _inputs():
         [os.path.join(ROOT, "include", "lbm.h"), __file__]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile liblbm.so (sm_103a) unless it is already up to date; return its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), debug: bool = False) -> str:
+    """Compile liblbm.so (sm_103a), or with debug=True liblbm_debug.so, unless it is up to date;
+    return its path."""
+    lib = LIB_DEBUG if debug else LIB
+    if not force and up_to_date(lib):
+        return lib
+    build_dir = os.path.join(BUILD, "debug") if debug else BUILD
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
+    if debug:
+        extra_flags = (*extra_flags, "-DLBM_BOUNDS_CHECK")
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         cmd = [cc, *ARCH, *FLAGS, *extra_flags, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -64,12 +73,12 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
 
     with ThreadPoolExecutor(max_workers=len(_sources())) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

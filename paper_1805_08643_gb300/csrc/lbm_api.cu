@@ -207,6 +207,7 @@ const char *lbm_status_string(int s) {
     case LBM_ERR_EOS_DOMAIN: return "LBM_ERR_EOS_DOMAIN";
     case LBM_ERR_TIMEOUT: return "LBM_ERR_TIMEOUT";
     case LBM_ERR_STATE: return "LBM_ERR_STATE";
+    case LBM_ERR_BOUNDS: return "LBM_ERR_BOUNDS";
     default: return "LBM_ERR_UNKNOWN";
   }
 }
@@ -336,7 +337,8 @@ lbm_status lbm_check(lbm_ctx *c) {
   CK(cudaMemcpyAsync(&w, err_word(c), sizeof(unsigned), cudaMemcpyDeviceToHost, c->L.stream), "read error word");
   CK(cudaMemsetAsync(err_word(c), 0, sizeof(unsigned), c->L.stream), "clear error word");
   CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
-  if (w & lbm::kErrTimeout) return fail(c, LBM_ERR_TIMEOUT, "a bounded wait for asynchronous copies gave up");
+  if (lbm::dbg::take_all()) return fail(c, LBM_ERR_BOUNDS, "a kernel index fell outside its buffer (debug build)");
+  if (w & lbm::kErrTimeout) return fail(c, LBM_ERR_TIMEOUT, "a bounded wait gave up");
   if (w & lbm::kErrNonFinite) return fail(c, LBM_ERR_NONFINITE, "non-finite density");
   if (w & lbm::kErrEosDomain) return fail(c, LBM_ERR_EOS_DOMAIN, "density left the domain of the EOS");
   return LBM_OK;
@@ -619,6 +621,26 @@ void lbm_destroy(lbm_ctx *c) {
 }
 
 }  // extern "C"
+
+// Registry of the debug build's per-translation-unit bounds-error readers
+// (empty in the normal build).
+namespace lbm {
+namespace dbg {
+static std::vector<unsigned (*)()> &readers() {
+  static std::vector<unsigned (*)()> r;
+  return r;
+}
+bool register_reader(unsigned (*r)()) {
+  readers().push_back(r);
+  return true;
+}
+unsigned take_all() {
+  unsigned v = 0;
+  for (auto r : readers()) v |= r();
+  return v;
+}
+}  // namespace dbg
+}  // namespace lbm
 
 // Read-only view of a context's parameters for other translation units.
 namespace lbm {

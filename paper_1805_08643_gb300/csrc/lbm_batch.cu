@@ -209,7 +209,7 @@ lbm_status rebuild(lbm_batch *b) {
         cudaError_t e = cudaMemsetAsync(b->d_done, 0, sizeof(int) * (size_t)b->ndone, b->stream);
         if (e != cudaSuccess) return e;
         return lbm::launch_batch_queue(b->precision, b->eos, b->d_boxes, b->d_items, b->nitems, parity, b->wl_grid,
-                                       b->d_done, b->d_err, b->stream);
+                                       b->d_done, (int)b->ndone, b->d_err, b->stream);
       }
       return b->pair ? lbm::launch_batch_pair(b->precision, b->eos, tile, b->d_boxes, b->d_items, b->nitems, parity,
                                               b->grid_blocks, pair_per_sm, b->d_err, b->stream)
@@ -480,6 +480,7 @@ lbm_status lbm_batch_check(lbm_batch *b) {
   BCK(cudaMemcpyAsync(&w, b->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream), "read error word");
   BCK(cudaMemsetAsync(b->d_err, 0, sizeof(unsigned), b->stream), "clear error word");
   BCK(cudaStreamSynchronize(b->stream), "sync");
+  if (lbm::dbg::take_all()) return bfail(b, LBM_ERR_BOUNDS, "a kernel index fell outside its buffer (debug build)");
   if (w & lbm::kErrTimeout) return bfail(b, LBM_ERR_TIMEOUT, "a bounded wait of the work-list step gave up");
   if (w & lbm::kErrNonFinite) return bfail(b, LBM_ERR_NONFINITE, "non-finite density");
   if (w & lbm::kErrEosDomain) return bfail(b, LBM_ERR_EOS_DOMAIN, "density left the domain of the EOS");

@@ -11,6 +11,7 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include "lbm_debug.cuh"
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -24,6 +25,9 @@ struct Nbhd {
   int self;
 
   __device__ __forceinline__ Nbhd(int x_, int y, int z, const KParams &P) {
+    x_ = LBM_IDX(x_, P.nx);  // debug build: the node must lie in the box
+    y = LBM_IDX(y, P.ny);
+    z = LBM_IDX(z, P.nz);
     x = x_;
     xm = x_ == 0 ? P.nx - 1 : x_ - 1;
     xp = x_ == P.nx - 1 ? 0 : x_ + 1;

@@ -216,7 +216,13 @@ int batch_tile_width(int nx);               // 64, 32 or 16: tiles of tw x (256 
 int batch_queue_tiles(const KParams &P);   // tile jobs per plane of a box in a batch work list
 cudaError_t batch_queue_grid(int precision, int eos, int *grid);
 cudaError_t launch_batch_queue(int precision, int eos, const BatchBox *boxes, const int4 *items, int nitems,
-                               int parity, int grid, int *done, unsigned *err, cudaStream_t s);
+                               int parity, int grid, int *done, int ndone, unsigned *err, cudaStream_t s);
+
+// Debug build (-DLBM_BOUNDS_CHECK): OR of the bounds-error words of every
+// translation unit, each cleared (synchronous); 0 in the normal build.
+namespace dbg {
+unsigned take_all();
+}
 
 size_t storage_bytes(int precision);  // bytes per stored population
 size_t psi_elem_bytes(int precision);

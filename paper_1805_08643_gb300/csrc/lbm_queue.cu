@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
       const int x = (t % G.ntx) * 2 * TXP + 2 * lane, y = (t / G.ntx) * kRows + row;
       if (x < P.nx && y < P.ny) fused_pair_at<S, OP, SIGMA, false>(g_in, g_out, psi_in, P, x, y, z, Rates<V2>(P));
       __syncthreads();
-      if (lane == 0 && row == 0) counter_release_add(done + z * G.T + t, 1);
+      if (lane == 0 && row == 0) counter_release_add(done + LBM_IDX(z * G.T + t, P.nz * G.T), 1);
     }
     if (it.z >= 0) {
       int z = it.z, t = it.w;
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
         zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
         xx = xx < 0 ? xx + G.ntx : (xx >= G.ntx ? xx - G.ntx : xx);
         yy = yy < 0 ? yy + G.nty : (yy >= G.nty ? yy - G.nty : yy);
-        const int *c = done + zz * G.T + yy * G.ntx + xx;
+        const int *c = done + LBM_IDX(zz * G.T + yy * G.ntx + xx, P.nz * G.T);
         const int target = stamp + P.wait_bias;
         for (int n = 0; counter_acquire(c) < target; ++n) {
           if (n >= P.spin_limit) {
@@ -196,7 +196,7 @@ __host__ __device__ inline BatchGeo batch_geo(const KParams &P, int tw) {
 template <typename S, int EOS>
 __global__ void __launch_bounds__(NTH, kMinBlocks)
     batch_queue_kernel(const BatchBox *__restrict__ boxes, const int4 *__restrict__ items, int nitems, int parity,
-                       int *__restrict__ done, unsigned *__restrict__ err) {
+                       int *__restrict__ done, int ndone, unsigned *__restrict__ err) {
   const int tid = threadIdx.y * TXP + threadIdx.x;
   unsigned e = 0;
 #pragma unroll 1
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
           fused_pair_at<S, kOrth, true, false>(gi, go, B.psi[in], P, x, y, z, Rates<V2>(P));
       }
       __syncthreads();
-      if (tid == 0) counter_release_add(done + B.qbase + z * G.T + t, 1);
+      if (tid == 0) counter_release_add(done + LBM_IDX(B.qbase + z * G.T + t, ndone), 1);
     }
     if (it.z >= 0) {
       const BatchBox &B = boxes[it.z];
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
         zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
         xx = xx < 0 ? xx + G.ntx : (xx >= G.ntx ? xx - G.ntx : xx);
         yy = yy < 0 ? yy + G.nty : (yy >= G.nty ? yy - G.nty : yy);
-        const int *c = done + B.qbase + zz * G.T + yy * G.ntx + xx;
+        const int *c = done + LBM_IDX(B.qbase + zz * G.T + yy * G.ntx + xx, ndone);
         const int target = 1 + P.wait_bias;  // counters are cleared before every launch
         for (int n = 0; counter_acquire(c) < target; ++n) {
           if (n >= P.spin_limit) {
@@ -255,20 +255,21 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
 
 template <typename S, int EOS>
 cudaError_t batch_launch(const BatchBox *boxes, const int4 *items, int nitems, int parity, int grid, int *done,
-                         unsigned *err, cudaStream_t s, int *per_sm) {
+                         int ndone, unsigned *err, cudaStream_t s, int *per_sm) {
   auto kern = batch_queue_kernel<S, EOS>;
   if (per_sm) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, NTH, 0);
-  void *args[] = {(void *)&boxes, (void *)&items, (void *)&nitems, (void *)&parity, (void *)&done, (void *)&err};
+  void *args[] = {(void *)&boxes, (void *)&items, (void *)&nitems, (void *)&parity,
+                  (void *)&done,  (void *)&ndone, (void *)&err};
   return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(TXP, kRows), args, 0, s);
 }
 
 template <typename S>
 cudaError_t batch_by_eos(int eos, const BatchBox *boxes, const int4 *items, int nitems, int parity, int grid,
-                         int *done, unsigned *err, cudaStream_t s, int *per_sm) {
+                         int *done, int ndone, unsigned *err, cudaStream_t s, int *per_sm) {
   switch (eos) {
-    case kEosCS: return batch_launch<S, kEosCS>(boxes, items, nitems, parity, grid, done, err, s, per_sm);
-    case kEosExp: return batch_launch<S, kEosExp>(boxes, items, nitems, parity, grid, done, err, s, per_sm);
-    default: return batch_launch<S, kEosNone>(boxes, items, nitems, parity, grid, done, err, s, per_sm);
+    case kEosCS: return batch_launch<S, kEosCS>(boxes, items, nitems, parity, grid, done, ndone, err, s, per_sm);
+    case kEosExp: return batch_launch<S, kEosExp>(boxes, items, nitems, parity, grid, done, ndone, err, s, per_sm);
+    default: return batch_launch<S, kEosNone>(boxes, items, nitems, parity, grid, done, ndone, err, s, per_sm);
   }
 }
 
@@ -452,8 +453,9 @@ bool batch_queue_items(const std::vector<const KParams *> &boxes, int grid, std:
 
 cudaError_t batch_queue_grid(int precision, int eos, int *grid) {
   int per_sm = 0, dev = 0, sms = 0;
-  cudaError_t e = precision == kF32 ? batch_by_eos<float>(eos, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, 0, &per_sm)
-                                    : batch_by_eos<__half>(eos, nullptr, nullptr, 0, 0, 0, nullptr, nullptr, 0, &per_sm);
+  cudaError_t e = precision == kF32
+                      ? batch_by_eos<float>(eos, nullptr, nullptr, 0, 0, 0, nullptr, 0, nullptr, 0, &per_sm)
+                      : batch_by_eos<__half>(eos, nullptr, nullptr, 0, 0, 0, nullptr, 0, nullptr, 0, &per_sm);
   if (e == cudaSuccess) e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
@@ -463,9 +465,11 @@ cudaError_t batch_queue_grid(int precision, int eos, int *grid) {
 }
 
 cudaError_t launch_batch_queue(int precision, int eos, const BatchBox *boxes, const int4 *items, int nitems,
-                               int parity, int grid, int *done, unsigned *err, cudaStream_t s) {
-  if (precision == kF32) return batch_by_eos<float>(eos, boxes, items, nitems, parity, grid, done, err, s, nullptr);
-  if (precision == kF16) return batch_by_eos<__half>(eos, boxes, items, nitems, parity, grid, done, err, s, nullptr);
+                               int parity, int grid, int *done, int ndone, unsigned *err, cudaStream_t s) {
+  if (precision == kF32)
+    return batch_by_eos<float>(eos, boxes, items, nitems, parity, grid, done, ndone, err, s, nullptr);
+  if (precision == kF16)
+    return batch_by_eos<__half>(eos, boxes, items, nitems, parity, grid, done, ndone, err, s, nullptr);
   return cudaErrorInvalidValue;
 }
 

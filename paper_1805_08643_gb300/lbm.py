@@ -14,9 +14,10 @@ from dataclasses import dataclass
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblbm.so")
+# LBM_DEBUG_LIBRARY=1: the debug build (kernel index checks, _build.build(debug=True))
+LIB_PATH = os.path.join(HERE, "liblbm_debug.so" if os.environ.get("LBM_DEBUG_LIBRARY") == "1" else "liblbm.so")
 
-OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_EOS_DOMAIN, ERR_TIMEOUT, ERR_STATE = range(8)
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_EOS_DOMAIN, ERR_TIMEOUT, ERR_STATE, ERR_BOUNDS = range(9)
 OPERATORS = {"orth": 0, "nonorth": 1, "nonorth_d3q15": 2}
 LATTICE_Q = {"orth": 19, "nonorth": 19, "nonorth_d3q15": 15}
 PRECISIONS = {"f64": 0, "f32": 1, "f16": 2}
