@@ -132,9 +132,21 @@ cudaEvent_t pooled_event(lbm_ctx *c) {
   return c->pool[c->pool_used++];
 }
 
-// Launch one kernel, bracketed by events while profiling is on.
+// NVTX name of a launch of the given kind (0: psi pass, 1: the step's other kernel).
+const char *launch_name(const lbm_ctx *c, int kind) {
+  if (kind == 0) return "lbm psi pass";
+  if (c->queued) return "lbm work-list step";
+  if (c->lagged) return "lbm trailing-psi single pass";
+  if (c->onchip) return "lbm on-chip-psi single pass";
+  if (c->onepass) return c->onepass_tma ? "lbm single pass (bulk copies)" : "lbm single pass";
+  return "lbm fused pass";
+}
+
+// Launch one kernel inside an NVTX range named for it, bracketed by events
+// while profiling is on.
 template <typename F>
 cudaError_t timed(lbm_ctx *c, int kind, F &&launch) {
+  const lbm::NvtxRange range(launch_name(c, kind));
   if (!c->profiling) return launch();
   cudaEvent_t a = pooled_event(c), b = pooled_event(c);
   if (!a || !b) return cudaErrorMemoryAllocation;

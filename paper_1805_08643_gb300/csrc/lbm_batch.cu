@@ -415,8 +415,13 @@ lbm_status lbm_batch_step(lbm_batch *b, int n) {
     if (s != LBM_OK) return s;
   }
   if (!b->nitems) return LBM_OK;
-  for (int k = 0; k + 1 < n; k += 2) BCK(cudaGraphLaunch(b->g2[b->phase], b->stream), "graph launch");
+  const char *name = b->wl ? "lbm batch work-list step" : b->pair ? "lbm batch two-pass step" : "lbm batch single pass";
+  for (int k = 0; k + 1 < n; k += 2) {
+    const lbm::NvtxRange range(name);  // one graph: two steps
+    BCK(cudaGraphLaunch(b->g2[b->phase], b->stream), "graph launch");
+  }
   if (n & 1) {
+    const lbm::NvtxRange range(name);
     BCK(cudaGraphLaunch(b->g1[b->phase], b->stream), "graph launch");
     b->phase ^= 1;  // every box's state is now at the other level
   }

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <vector>
@@ -58,6 +59,15 @@ struct KParams {
 };
 
 constexpr int kDefaultSpinLimit = 1 << 22;
+
+// An NVTX range around a scope (a kernel launch, a graph launch): visible in
+// profilers that trace NVTX; a cheap no-op otherwise.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Layout of the scratch buffer.
 constexpr int kReduceBlocks = 1024;
