@@ -75,7 +75,7 @@ HEADLINE = ("nonorth", "f32")
 FUSED_DRAM_BYTES = {("nonorth", "f32"): 152.6, ("nonorth", "f16"): 77.4}
 # DRAM bytes per node of one launch of the work-list single pass at 256^3 (ncu dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch over the nodes)
-QUEUE_DRAM_BYTES = {}
+QUEUE_DRAM_BYTES = {("nonorth", "f32"): 173.7}
 # FP64 instructions per node of the fused pass (ncu instruction counts at 128^3 over the nodes) and the FP64
 # issue peak of one GB300: 2 per SM per clock x 152 SMs x 2070 MHz.
 FUSED_FP64_INSTR = {"nonorth": 255.0, "orth": 309.0, "nonorth_d3q15": 207.0}
@@ -349,27 +349,39 @@ def served_run(n_jobs=24, load=1.0, max_steps=2000, tol=1e-7):
     return out
 
 
-def serve_study(n_jobs=40, loads=(0.5, 1.0, 2.0), max_steps=2000, tol=1e-8):
+def serve_study(n_jobs=200, loads=(0.25, 0.5, 1.0, 1.5, 2.0), max_steps=100_000, tol=1e-8, pilot_jobs=32):
     """The served configuration: Poisson streams of droplet / slab jobs, box edges U[48, 192], T/T_c U[0.6, 0.9],
-    random operator, FP32, run until max|du| < tol per 100 steps (or max_steps); offered rate swept as multiples
-    of a capacity estimate (20 GLUPS over jobs of mean edge^3 x max_steps).  p50 / p99 time from arrival to
-    convergence and aggregate MLUPS per rate."""
+    random operator, FP32, run until max|du| < tol per 100 steps (converged) or max_steps (truncated, reported
+    apart); offered rate swept as multiples of the measured service capacity.  Capacity: a pilot of
+    `pilot_jobs` jobs of the same distribution (another seed), all present at the start, served to completion:
+    jobs / wall time.  Per rate: p50 / p99 arrival-to-convergence latency, truncated jobs, aggregate MLUPS."""
     from paper_1805_08643_gb300 import synth
     from paper_1805_08643_gb300.serve import BatchBackend, Server
 
     lo, hi = 48, 192
-    mean_nodes = (hi ** 4 - lo ** 4) / (4 * (hi - lo))
-    capacity = 20e9 / (mean_nodes * max_steps)
+    budget = 96 << 30
+    t0 = time.perf_counter()
+    pilot = synth.job_stream(pilot_jobs, rate_per_s=1e9, edge_lo=lo, edge_hi=hi, seed=synth.SEED + 1)
+    be = BatchBackend("f32", hbm_budget_bytes=budget)
+    prep = Server(be, check_every=100, tol=tol, max_steps=max_steps, min_steps=200).run(pilot)
+    be.close()
+    capacity = pilot_jobs / prep.wall_s
     rows = []
     for load in loads:
+        if n_jobs < 1:
+            break
         jobs = synth.job_stream(n_jobs, rate_per_s=load * capacity, edge_lo=lo, edge_hi=hi)
-        be = BatchBackend("f32", hbm_budget_bytes=96 << 30)
+        be = BatchBackend("f32", hbm_budget_bytes=budget)
         rep = Server(be, check_every=100, tol=tol, max_steps=max_steps, min_steps=200).run(jobs)
         be.close()
         rows.append({"load": load, "offered_jobs_per_s": load * capacity, **rep.summary()})
+        print(json.dumps({"progress": rows[-1]}), file=sys.stderr, flush=True)
     return {"study": "serve", "jobs_per_rate": n_jobs, "edge": [lo, hi], "tol_max_du_per_100_steps": tol,
-            "max_steps": max_steps, "workload": "droplet or slab, T/Tc U[0.6,0.9], operator random, FP32, a=0.25, "
-                                                "W=5, sigma=0.105 (droplet) / 0.116 (slab)", "rates": rows}
+            "max_steps": max_steps, "capacity_jobs_per_s": capacity,
+            "pilot": {"jobs": pilot_jobs, **prep.summary()},
+            "workload": "droplet or slab, T/Tc U[0.6,0.9], operator random, FP32, a=0.25, W=5, "
+                        "sigma=0.105 (droplet) / 0.116 (slab)", "rates": rows,
+            "seconds": time.perf_counter() - t0}
 
 
 def precision_study(edge=512, steps=5000):
@@ -699,6 +711,9 @@ def main():
     ap.add_argument("--study", default=None, choices=["precision", "serve"],
                     help="run a study instead of the benchmark line (minutes)")
     ap.add_argument("--study-steps", type=int, default=5000)
+    ap.add_argument("--serve-jobs", type=int, default=200, help="jobs per offered rate of --study serve")
+    ap.add_argument("--serve-loads", default="0.25,0.5,1,1.5,2",
+                    help="offered rates of --study serve, as multiples of the measured capacity")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -720,7 +735,8 @@ def main():
         return
     if args.study == "serve":
         if rank == 0:
-            print(json.dumps(serve_study()))
+            print(json.dumps(serve_study(n_jobs=args.serve_jobs,
+                                         loads=tuple(float(v) for v in args.serve_loads.split(",")))))
         return
     n = args.edge ** 3
     hbm_peak, peak_kind = peaks()

@@ -63,6 +63,7 @@ struct lbm_batch {
   bool dirty = true;         // descriptors / items need uploading, graphs re-capturing
   bool pair = false;         // the captured step is the two-pass pair kernels
   bool wl = false;           // ... or the work-list single pass
+  bool odd = false;          // ... and the one-node single pass for the odd-Nx boxes
   int *d_done = nullptr;     // its completion counters, cleared before every launch
   long long cap_done = 0, ndone = 0;
   int wl_grid = 0;
@@ -127,31 +128,47 @@ lbm_status rebuild(lbm_batch *b) {
     if (b->boxes[i].live && b->boxes[i].initialised) order.push_back({(long long)b->boxes[i].d.P.n, i});
   }
   std::sort(order.begin(), order.end(), [](auto &x, auto &y) { return x.first > y.first || (x.first == y.first && x.second < y.second); });
-  bool pair = true;
-  for (auto &o : order) pair = pair && b->boxes[o.second].d.P.nx % 2 == 0;
-  const bool wl = pair && b->tile == kTileWorkList;
+  // boxes with an even Nx step on the two-node kernels (the work list, or the two-pass pair kernels);
+  // boxes with an odd Nx on the one-node single pass; one step graph runs both groups
+  std::vector<std::pair<long long, int>> even, odd;
+  for (auto &o : order) (b->boxes[o.second].d.P.nx % 2 == 0 ? even : odd).push_back(o);
+  const bool wl = !even.empty() && b->tile == kTileWorkList;
+  const int tile = b->tile == kTileWorkList ? lbm::kTile32x8 : b->tile;  // of the tile-shaped kernels
   std::vector<int4> items;
+  auto tile_items = [&](const std::vector<std::pair<long long, int>> &group) {
+    int bx, by;
+    lbm::onepass_tile_shape(tile, &bx, &by);
+    for (auto &o : group) {
+      const HostBox &h = b->boxes[o.second];
+      const KParams &P = h.d.P;
+      const int tx = (P.nx + bx - 1) / bx, ty = (P.ny + by - 1) / by, zc = h.zc > 0 ? h.zc : default_zc(P);
+      for (int z0 = 0; z0 < P.nz; z0 += zc)
+        for (int j = 0; j < ty; ++j)
+          for (int i = 0; i < tx; ++i)
+            items.push_back(make_int4(o.second, i | (j << 16), z0, std::min(z0 + zc, P.nz)));
+    }
+  };
   if (wl) {
-    // the work list over the boxes in this order; each box's counters start at its qbase
+    // the work list over the even-Nx boxes in this order; each box's counters start at its qbase
     BCK(lbm::batch_queue_grid(b->precision, b->eos, &b->wl_grid), "work list occupancy");
     std::vector<const KParams *> ps;
-    for (auto &o : order) ps.push_back(&b->boxes[o.second].d.P);
+    for (auto &o : even) ps.push_back(&b->boxes[o.second].d.P);
     std::vector<int> base;
     long long nc = 0;
     if (!lbm::batch_queue_items(ps, b->wl_grid, items, base, &nc)) return bfail(b, LBM_ERR_ARG, "no valid work list");
-    for (size_t k = 0; k < order.size(); ++k) {
-      BatchBox &d = b->boxes[order[k].second].d;
+    for (size_t k = 0; k < even.size(); ++k) {
+      BatchBox &d = b->boxes[even[k].second].d;
       d.qbase = base[k];
       d.tw = lbm::batch_tile_width(d.P.nx);
-      desc[order[k].second].qbase = d.qbase;
-      desc[order[k].second].tw = d.tw;
+      desc[even[k].second].qbase = d.qbase;
+      desc[even[k].second].tw = d.tw;
     }
-    // the list numbers boxes in `order`; the kernel reads the descriptor table by slot: renumber, then
+    // the list numbers boxes in `even`; the kernel reads the descriptor table by slot: renumber, then
     // check every job against the descriptor it will read (plane and tile inside that box, counter
     // inside the counter array)
     for (auto &it : items) {
-      if (it.x >= 0) it.x = order[it.x].second;
-      if (it.z >= 0) it.z = order[it.z].second;
+      if (it.x >= 0) it.x = even[it.x].second;
+      if (it.z >= 0) it.z = even[it.z].second;
       for (int side = 0; side < 2; ++side) {
         const int slot = side ? it.z : it.x;
         if (slot < 0) continue;
@@ -159,7 +176,8 @@ lbm_status rebuild(lbm_batch *b) {
         const unsigned zt = (unsigned)(side ? it.w : it.y);
         const long long z = zt & 0xffffu, t = zt >> 16;
         const long long T = lbm::batch_queue_tiles(P);
-        if (slot >= nb || !b->boxes[slot].live || z >= P.nz || t >= T || desc[slot].qbase + P.nz * T > nc)
+        if (slot >= nb || !b->boxes[slot].live || P.nx % 2 != 0 || z >= P.nz || t >= T ||
+            desc[slot].qbase + P.nz * T > nc)
           return bfail(b, LBM_ERR_ARG, "work list does not match the box table");
       }
     }
@@ -171,18 +189,10 @@ lbm_status rebuild(lbm_batch *b) {
     }
     b->ndone = nc;
   } else {
-    int bx, by;
-    lbm::onepass_tile_shape(b->tile == kTileWorkList ? lbm::kTile32x8 : b->tile, &bx, &by);
-    for (auto &o : order) {
-      const HostBox &h = b->boxes[o.second];
-      const KParams &P = h.d.P;
-      const int tx = (P.nx + bx - 1) / bx, ty = (P.ny + by - 1) / by, zc = h.zc > 0 ? h.zc : default_zc(P);
-      for (int z0 = 0; z0 < P.nz; z0 += zc)
-        for (int j = 0; j < ty; ++j)
-          for (int i = 0; i < tx; ++i)
-            items.push_back(make_int4(o.second, i | (j << 16), z0, std::min(z0 + zc, P.nz)));
-    }
+    tile_items(even);
   }
+  const int n_even = (int)items.size();
+  tile_items(odd);
   if ((int)items.size() > b->cap_items) {
     if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
     BCK(cudaMallocAsync((void **)&b->d_items, sizeof(int4) * items.size(), b->stream), "item table");
@@ -194,27 +204,32 @@ lbm_status rebuild(lbm_batch *b) {
     BCK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, b->stream), "H2D items");
   BCK(cudaStreamSynchronize(b->stream), "sync");  // host vectors go out of scope
   destroy_graphs(b);
-  b->pair = pair && !wl;
   b->wl = wl;
+  b->pair = !wl && n_even > 0;
+  b->odd = b->nitems > n_even;
   if (b->nitems) {
     // resident blocks per SM: the pair kernels' own occupancy (the psi kernel needs half the fused kernel's
     // registers), the single-pass kernel's launch bounds
-    const int tile = b->tile == kTileWorkList ? lbm::kTile32x8 : b->tile;
     int pair_per_sm[2] = {1, 1};
     if (b->pair) BCK(lbm::batch_pair_occupancy(b->precision, b->eos, tile, pair_per_sm), "pair kernel occupancy");
     const int per_sm = tile == lbm::kTile32x4 ? 4 : 2;
-    const int grid = std::min(b->grid_blocks * per_sm, b->nitems);
+    const int n_odd = b->nitems - n_even;
+    const int grid_odd = std::min(b->grid_blocks * per_sm, std::max(n_odd, 1));
     auto step = [&](int parity) {
+      cudaError_t e = cudaSuccess;
       if (wl) {
-        cudaError_t e = cudaMemsetAsync(b->d_done, 0, sizeof(int) * (size_t)b->ndone, b->stream);
-        if (e != cudaSuccess) return e;
-        return lbm::launch_batch_queue(b->precision, b->eos, b->d_boxes, b->d_items, b->nitems, parity, b->wl_grid,
-                                       b->d_done, (int)b->ndone, b->d_err, b->stream);
+        e = cudaMemsetAsync(b->d_done, 0, sizeof(int) * (size_t)b->ndone, b->stream);
+        if (e == cudaSuccess)
+          e = lbm::launch_batch_queue(b->precision, b->eos, b->d_boxes, b->d_items, n_even, parity, b->wl_grid,
+                                      b->d_done, (int)b->ndone, b->d_err, b->stream);
+      } else if (n_even) {
+        e = lbm::launch_batch_pair(b->precision, b->eos, tile, b->d_boxes, b->d_items, n_even, parity,
+                                   b->grid_blocks, pair_per_sm, b->d_err, b->stream);
       }
-      return b->pair ? lbm::launch_batch_pair(b->precision, b->eos, tile, b->d_boxes, b->d_items, b->nitems, parity,
-                                              b->grid_blocks, pair_per_sm, b->d_err, b->stream)
-                     : lbm::launch_batch_onepass(b->precision, b->eos, tile, b->d_boxes, b->d_items, b->nitems,
-                                                 parity, grid, b->d_err, b->stream);
+      if (e == cudaSuccess && n_odd)
+        e = lbm::launch_batch_onepass(b->precision, b->eos, tile, b->d_boxes, b->d_items + n_even, n_odd, parity,
+                                      grid_odd, b->d_err, b->stream);
+      return e;
     };
     for (int k = 0; k < 4; ++k) {  // g2[0], g2[1], g1[0], g1[1]
       const int two = k < 2, p0 = k & 1;
@@ -415,7 +430,9 @@ lbm_status lbm_batch_step(lbm_batch *b, int n) {
     if (s != LBM_OK) return s;
   }
   if (!b->nitems) return LBM_OK;
-  const char *name = b->wl ? "lbm batch work-list step" : b->pair ? "lbm batch two-pass step" : "lbm batch single pass";
+  const char *name = b->wl ? (b->odd ? "lbm batch work-list + single pass (odd Nx)" : "lbm batch work-list step")
+                    : b->pair ? (b->odd ? "lbm batch two-pass + single pass (odd Nx)" : "lbm batch two-pass step")
+                              : "lbm batch single pass";
   for (int k = 0; k + 1 < n; k += 2) {
     const lbm::NvtxRange range(name);  // one graph: two steps
     BCK(cudaGraphLaunch(b->g2[b->phase], b->stream), "graph launch");

@@ -4,9 +4,10 @@ Jobs (a box size, a droplet or a liquid slab, a reduced temperature, an
 operator) arrive over time.  The server keeps every admitted job's populations
 resident on the device inside one batch (include/lbm.h, "batches"), admits a
 waiting job as soon as the batch's HBM budget has room for it, advances all
-running jobs together with one persistent launch per step, and retires a job
+running jobs together (one step graph per check interval), and retires a job
 when its velocity field has converged: max |u(t) - u(t - check_every)| below
-``tol`` (or at ``max_steps``).  Latency is arrival to retirement.
+``tol``, or when it reaches ``max_steps`` (reported apart, as truncated).
+Latency is arrival to retirement.
 
 The scheduling logic is independent of the device: ``Server`` drives any
 backend with the ``BatchBackend`` interface, which the tests replace with a
@@ -33,6 +34,7 @@ class JobState:
     done_at: float | None = None
     steps: int = 0
     last_du: float | None = None
+    converged: bool | None = None  # at retirement: converged, or stopped at max_steps
 
 
 class BatchBackend:
@@ -84,23 +86,36 @@ class BatchBackend:
         self.batch.close()
 
 
+def _percentile(values, q):
+    if not values:
+        return None
+    xs = sorted(values)
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
 @dataclass
 class ServeReport:
-    latencies_s: list = field(default_factory=list)
+    latencies_s: list = field(default_factory=list)            # jobs that converged
+    truncated_latencies_s: list = field(default_factory=list)  # jobs retired at max_steps
+    converged_steps: list = field(default_factory=list)
     lattice_updates: int = 0
     wall_s: float = 0.0
     max_running: int = 0
     jobs: list = field(default_factory=list)
 
     def percentile(self, q):
-        if not self.latencies_s:
-            return None
-        xs = sorted(self.latencies_s)
-        k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
-        return xs[k]
+        """Arrival-to-convergence latency percentile over the converged jobs."""
+        return _percentile(self.latencies_s, q)
 
     def summary(self):
-        return {"jobs": len(self.latencies_s), "p50_s": self.percentile(50), "p99_s": self.percentile(99),
+        both = self.latencies_s + self.truncated_latencies_s
+        steps = self.converged_steps
+        return {"jobs": len(both), "converged": len(self.latencies_s),
+                "truncated": len(self.truncated_latencies_s),
+                "p50_s": self.percentile(50), "p99_s": self.percentile(99),
+                "p50_all_s": _percentile(both, 50), "p99_all_s": _percentile(both, 99),
+                "mean_steps_to_converge": sum(steps) / len(steps) if steps else None,
                 "aggregate_mlups": self.lattice_updates / self.wall_s / 1e6 if self.wall_s > 0 else None,
                 "wall_s": self.wall_s, "max_running": self.max_running}
 
@@ -154,9 +169,15 @@ class Server:
             keep = []
             for j, d in zip(running, du):
                 j.last_du = d
-                if (j.steps >= self.min_steps and d < self.tol) or j.steps >= self.max_steps:
+                converged = j.steps >= self.min_steps and d < self.tol
+                if converged or j.steps >= self.max_steps:
                     j.done_at = now
-                    report.latencies_s.append(now - j.spec.arrival)
+                    j.converged = converged
+                    if converged:
+                        report.latencies_s.append(now - j.spec.arrival)
+                        report.converged_steps.append(j.steps)
+                    else:
+                        report.truncated_latencies_s.append(now - j.spec.arrival)
                     if on_retire:
                         on_retire(j)
                     self.backend.release(j.box)

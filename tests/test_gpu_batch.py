@@ -250,3 +250,23 @@ def test_work_list_batch_against_the_oracle_and_join_leave():
     f0 = L.equilibrium_state(po, droplet_rho(grid, centre, min(grid) / 4, W, rl, rv))
     rho_o, u_o, _, _ = L.macroscopic(po, L.run(po, f0, 12))
     assert max_abs(rho, rho_o) <= 2e-5 and max_abs(u, u_o) <= 2e-5
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_odd_and_even_boxes_in_one_batch_each_step_as_alone(prec):
+    """A batch holding odd- and even-Nx boxes steps the even ones on the work list and the odd ones on the
+    one-node single pass, in one graph: each box's result equals the box stepped alone, bit for bit."""
+    mix = [((25, 20, 28), "orth", 0.8, 0.105, 2.0), BOXES[0], ((33, 30, 26), "nonorth", 0.75, 0.0, 3.0), BOXES[2]]
+    b = _batch(prec)
+    ids = [_add(b, s, prec) for s in mix]
+    b.step(9)
+    assert b.check() == 0
+    got = [b.moments(i) for i in ids]
+    b.close()
+    for spec, (r, u) in zip(mix, got):
+        alone = _batch(prec)
+        i = _add(alone, spec, prec)
+        alone.step(9)
+        r1, u1 = alone.moments(i)
+        alone.close()
+        assert np.array_equal(r, r1) and np.array_equal(u, u1), spec

@@ -42,4 +42,5 @@ def test_admission_waits_for_room():
     jobs = [JobSpec(0.0, 32, "droplet", 0.8, "nonorth") for _ in range(5)]
     rep = Server(be, check_every=100, tol=0.0, max_steps=200, keep_jobs=True).run(jobs)
     be.close()
-    assert len(rep.latencies_s) == 5 and rep.max_running == 2
+    s = rep.summary()  # tol = 0: every job stops at max_steps and counts as truncated
+    assert s["jobs"] == 5 and s["truncated"] == 5 and s["converged"] == 0 and rep.max_running == 2

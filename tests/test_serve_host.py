@@ -82,3 +82,19 @@ def test_jobs_arriving_later_join_running_ones():
     rep = Server(be, check_every=100, clock=clock, sleep=clock.sleep, keep_jobs=True).run(jobs)
     a, b = sorted(rep.jobs, key=lambda j: j.spec.arrival)
     assert b.admitted_at < a.done_at  # the second job ran while the first was still on the device
+
+
+def test_truncated_jobs_are_reported_apart_from_converged_ones():
+    """Jobs stopped at max_steps do not enter the convergence latencies."""
+    clock = FakeClock()
+    jobs = job_stream(12, rate_per_s=100.0, edge_lo=48, edge_hi=144, seed=5)
+    be = FakeBackend(clock, budget=4 * 144 ** 3)
+    # converge needs 300 * edge / 48 steps: edges above 64 need more than max_steps = 400
+    rep = Server(be, check_every=100, tol=1e-8, max_steps=400, min_steps=200, clock=clock,
+                 sleep=clock.sleep, keep_jobs=True).run(jobs)
+    s = rep.summary()
+    want_conv = sum(1 for j in jobs if 300 * j.edge / 48 <= 400)
+    assert s["converged"] == want_conv and s["truncated"] == len(jobs) - want_conv and s["jobs"] == len(jobs)
+    assert all(j.converged == (300 * j.spec.edge / 48 <= 400) for j in rep.jobs)
+    assert all(st <= 400 for st in rep.converged_steps)
+    assert s["p50_all_s"] is not None
