@@ -349,23 +349,28 @@ def served_run(n_jobs=24, load=1.0, max_steps=2000, tol=1e-7):
     return out
 
 
-def serve_study(n_jobs=200, loads=(0.25, 0.5, 1.0, 1.5, 2.0), max_steps=100_000, tol=1e-8, pilot_jobs=32):
+def serve_study(n_jobs=200, loads=(0.25, 0.5, 1.0, 1.5, 2.0), max_steps=100_000, tol=1e-8, pilot_jobs=32,
+                capacity=None):
     """The served configuration: Poisson streams of droplet / slab jobs, box edges U[48, 192], T/T_c U[0.6, 0.9],
     random operator, FP32, run until max|du| < tol per 100 steps (converged) or max_steps (truncated, reported
     apart); offered rate swept as multiples of the measured service capacity.  Capacity: a pilot of
     `pilot_jobs` jobs of the same distribution (another seed), all present at the start, served to completion:
-    jobs / wall time.  Per rate: p50 / p99 arrival-to-convergence latency, truncated jobs, aggregate MLUPS."""
+    jobs / wall time (or `capacity` jobs/s, from an earlier pilot).  Per rate: p50 / p99 arrival-to-convergence
+    latency, truncated jobs, aggregate MLUPS."""
     from paper_1805_08643_gb300 import synth
     from paper_1805_08643_gb300.serve import BatchBackend, Server
 
     lo, hi = 48, 192
     budget = 96 << 30
     t0 = time.perf_counter()
-    pilot = synth.job_stream(pilot_jobs, rate_per_s=1e9, edge_lo=lo, edge_hi=hi, seed=synth.SEED + 1)
-    be = BatchBackend("f32", hbm_budget_bytes=budget)
-    prep = Server(be, check_every=100, tol=tol, max_steps=max_steps, min_steps=200).run(pilot)
-    be.close()
-    capacity = pilot_jobs / prep.wall_s
+    pilot_summary = None
+    if capacity is None:
+        pilot = synth.job_stream(pilot_jobs, rate_per_s=1e9, edge_lo=lo, edge_hi=hi, seed=synth.SEED + 1)
+        be = BatchBackend("f32", hbm_budget_bytes=budget)
+        prep = Server(be, check_every=100, tol=tol, max_steps=max_steps, min_steps=200).run(pilot)
+        be.close()
+        capacity = pilot_jobs / prep.wall_s
+        pilot_summary = {"jobs": pilot_jobs, **prep.summary()}
     rows = []
     for load in loads:
         if n_jobs < 1:
@@ -378,7 +383,7 @@ def serve_study(n_jobs=200, loads=(0.25, 0.5, 1.0, 1.5, 2.0), max_steps=100_000,
         print(json.dumps({"progress": rows[-1]}), file=sys.stderr, flush=True)
     return {"study": "serve", "jobs_per_rate": n_jobs, "edge": [lo, hi], "tol_max_du_per_100_steps": tol,
             "max_steps": max_steps, "capacity_jobs_per_s": capacity,
-            "pilot": {"jobs": pilot_jobs, **prep.summary()},
+            "pilot": pilot_summary,
             "workload": "droplet or slab, T/Tc U[0.6,0.9], operator random, FP32, a=0.25, W=5, "
                         "sigma=0.105 (droplet) / 0.116 (slab)", "rates": rows,
             "seconds": time.perf_counter() - t0}
@@ -712,6 +717,8 @@ def main():
                     help="run a study instead of the benchmark line (minutes)")
     ap.add_argument("--study-steps", type=int, default=5000)
     ap.add_argument("--serve-jobs", type=int, default=200, help="jobs per offered rate of --study serve")
+    ap.add_argument("--serve-capacity", type=float, default=None,
+                    help="service capacity (jobs/s) of --study serve; default: measure it with a pilot")
     ap.add_argument("--serve-loads", default="0.25,0.5,1,1.5,2",
                     help="offered rates of --study serve, as multiples of the measured capacity")
     args = ap.parse_args()
@@ -736,7 +743,8 @@ def main():
     if args.study == "serve":
         if rank == 0:
             print(json.dumps(serve_study(n_jobs=args.serve_jobs,
-                                         loads=tuple(float(v) for v in args.serve_loads.split(",")))))
+                                         loads=tuple(float(v) for v in args.serve_loads.split(",")),
+                                         capacity=args.serve_capacity)))
         return
     n = args.edge ** 3
     hbm_peak, peak_kind = peaks()
