@@ -139,7 +139,7 @@ cudaError_t launch_onepass(const KParams &P, int precision, int op, bool sigma, 
 // One box of a batch as the batched kernel sees it (copied to shared memory
 // per work item).  g[k] / psi[k]: the two time levels; cur: which level holds
 // the state at the batch's parity 0.
-struct BatchBox {
+struct alignas(16) BatchBox {  // 16-byte aligned: copied to shared memory in 16-byte pieces
   KParams P;
   void *g[2];
   float *psi[2];

@@ -172,8 +172,9 @@ cudaError_t occupancy_of(int *per_sm) {
 
 // ------------------------------------------------------------------ batches
 // The same work list over many boxes.  Every job carries its box, whose
-// descriptor (parameters, buffers, operator, level, tile width) the threads
-// read from global memory through the read-only path; a fused job of box B
+// descriptor (parameters, buffers, operator, level, tile width) the block
+// copies to shared memory one item ahead (asynchronous copies, double
+// buffered), so it is there when the item starts; a fused job of box B
 // reads level in = B.cur ^ parity and writes in ^ 1, the psi job evaluates psi
 // of level in ^ 1.  Both operators and the Eq. 16 term (zero coefficient when
 // off) are compiled in.  Tiles are tw x (256 / tw) nodes, tw = 64, 32 or 16 per
@@ -193,17 +194,45 @@ __host__ __device__ inline BatchGeo batch_geo(const KParams &P, int tw) {
   return g;
 }
 
+// Copy box descriptors to shared memory with asynchronous 16-byte copies (one
+// commit group per call), so that the next item's descriptors arrive while the
+// current item runs.
+__device__ __forceinline__ void prefetch_boxes(BatchBox *dst, const BatchBox *__restrict__ boxes, int4 it, int tid) {
+  constexpr int chunks = (int)(sizeof(BatchBox) / 16);
+  static_assert(sizeof(BatchBox) % 16 == 0, "descriptor copies move 16-byte pieces");
+  for (int side = 0; side < 2; ++side) {
+    const int box = side ? it.z : it.x;
+    if (box < 0) continue;
+    const char *src = (const char *)(boxes + box);
+    char *d = (char *)(dst + side);
+    for (int c = tid; c < chunks; c += NTH) {
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(d + 16 * c);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src + 16 * c) : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <typename S, int EOS>
 __global__ void __launch_bounds__(NTH, kMinBlocks)
     batch_queue_kernel(const BatchBox *__restrict__ boxes, const int4 *__restrict__ items, int nitems, int parity,
                        int *__restrict__ done, int ndone, unsigned *__restrict__ err) {
+  __shared__ BatchBox bb[2][2];  // [item parity][fused job's box, psi job's box]
   const int tid = threadIdx.y * TXP + threadIdx.x;
   unsigned e = 0;
+  int k = blockIdx.x;
+  int4 it = k < nitems ? __ldg(items + k) : make_int4(-1, -1, -1, -1);
+  prefetch_boxes(bb[0], boxes, it, tid);
 #pragma unroll 1
-  for (int k = blockIdx.x; k < nitems; k += gridDim.x) {
-    const int4 it = __ldg(items + k);
+  for (int i = 0; k < nitems; ++i, k += gridDim.x) {
+    const int kn = k + gridDim.x;
+    const int4 next = kn < nitems ? __ldg(items + kn) : make_int4(-1, -1, -1, -1);
+    __syncthreads();  // every thread is done with the buffer the next copies overwrite
+    prefetch_boxes(bb[(i + 1) & 1], boxes, next, tid);
+    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this item's descriptors have arrived
+    __syncthreads();
     if (it.x >= 0) {
-      const BatchBox &B = boxes[it.x];
+      const BatchBox &B = bb[i & 1][0];
       const KParams &P = B.P;
       const BatchGeo G = batch_geo(P, B.tw);
       int z = (int)((unsigned)it.y & 0xffffu), t = (int)((unsigned)it.y >> 16);
@@ -222,7 +251,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
       if (tid == 0) counter_release_add(done + LBM_IDX(B.qbase + z * G.T + t, ndone), 1);
     }
     if (it.z >= 0) {
-      const BatchBox &B = boxes[it.z];
+      const BatchBox &B = bb[i & 1][1];
       const KParams &P = B.P;
       const BatchGeo G = batch_geo(P, B.tw);
       int z = (int)((unsigned)it.w & 0xffffu), t = (int)((unsigned)it.w >> 16);
@@ -249,7 +278,9 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
       const int x = tx * G.tw + 2 * (tid % half), y = ty * G.th + tid / half;
       if (x < P.nx && y < P.ny) psi_pair_at_l2<S, EOS, false>((const S *)B.g[in ^ 1], B.psi[in ^ 1], P, x, y, z, e);
     }
+    it = next;
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the block
   if (e) atomicOr(err, e);
 }
 
