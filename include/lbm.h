@@ -68,8 +68,9 @@ typedef enum {
  * zero for e_x e_y e_z), rates 1, s_e, s_nu x5, s_q x4, s_pi, and Eq. 15 weights
  * 1/3 (axes), 1/24 (corners).  A D3Q15 context runs the two-pass step (the
  * two-node kernels for the FP32-arithmetic forms with an even Nx, the one-node
- * kernels otherwise); the single-pass variants (lbm_set_tuning), the no-alloc
- * step (lbm_step_static) and batches are D3Q19 only. */
+ * kernels otherwise) or, for those forms, the work-list step (mode 5 of
+ * lbm_set_tuning; the default with LBM_F32 storage); the other single-pass
+ * variants, the no-alloc step (lbm_step_static) and batches are D3Q19 only. */
 typedef enum {
   LBM_OP_ORTHOGONAL = 0,
   LBM_OP_NONORTHOGONAL = 1,
@@ -183,8 +184,8 @@ lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
                             double *ms_fused, long long *n_fused);
 
 /* Kernel choice for this context.  The default is 5 (below) for an LBM_F32
- * D3Q19 context with an even Nx, the faster step there on GB300, and 0
- * otherwise.  single_pass = 0 runs the psi pass and the fused pass.  1 (LBM_F32 and LBM_F32_STORE_F16 only) runs each
+ * context with an even Nx (D3Q19 or D3Q15), the faster step there on GB300,
+ * and 0 otherwise.  single_pass = 0 runs the psi pass and the fused pass.  1 (LBM_F32 and LBM_F32_STORE_F16 only) runs each
  * step as one kernel that also produces psi of the next step, recomputing
  * collisions on a one-node ring around each thread block's tile.  2 runs that
  * single pass with its data moved by bulk asynchronous copies (LBM_F32 only,
@@ -198,20 +199,20 @@ lbm_status lbm_kernel_times(lbm_ctx *ctx, double *ms_psi, long long *n_psi,
  * pass of the next step trails the fused pass by one plane, reading the new
  * populations from L2; results equal the two-pass step bit for bit; the first
  * call in this mode allocates a small device array of progress flags (one int
- * per 64x4 tile and plane), freed by lbm_destroy.  5 (same forms, D3Q19)
- * runs each step as one cooperative launch over an ordered work list: each
+ * per 64x4 tile and plane), freed by lbm_destroy.  5 (same forms; also
+ * on D3Q15) runs each step as one cooperative launch over an ordered work list: each
  * item is the fused pass of one 64x4 tile of one plane plus the psi pass of
  * the next step for another tile, placed (and checked, on the host) at least
- * one wave of the grid after the 27 fused tiles it reads; the FP64 EOS of the
+ * half a wave of the grid after the 27 fused tiles it reads; the FP64 EOS of the
  * psi work overlaps the fused work's HBM stream and the populations it pulls
- * come from L2 (Eqs. 3-6 in 2 x 19 x s + 8 bytes per node); results equal the
+ * come from L2 (Eqs. 3-6 in 2 x Q x s + 8 bytes per node); results equal the
  * two-pass step bit for bit; the first step in this mode allocates the item
  * table and counters (about 20 bytes per tile and plane), freed by
  * lbm_destroy.  tile picks the x-y tile of
  * the single-pass kernel (0: 32x4, 1: 32x8, 2: 64x4); z_planes the z planes
  * each thread block marches through (0 = automatic).  Results do not depend on
  * tile or z_planes.  Errors: LBM_ERR_ARG (bad value, a mode the context's
- * precision or Nx does not support, or a single-pass mode on a D3Q15 context);
+ * precision or Nx does not support, or a single-pass mode other than 5 on a D3Q15 context);
  * LBM_ERR_OOM / LBM_ERR_CUDA (mode 4's flag array or mode 5's item table
  * could not be allocated, at the first step in mode 5). */
 lbm_status lbm_set_tuning(lbm_ctx *ctx, int single_pass, int tile, int z_planes);

@@ -540,7 +540,8 @@ lbm_status lbm_set_tuning(lbm_ctx *c, int single_pass, int tile, int z_planes) {
   if (!c || single_pass < 0 || single_pass > 5 || tile < 0 || tile > 2 || z_planes < 0)
     return fail(c, LBM_ERR_ARG, "bad tuning");
   if (single_pass && c->precision == LBM_F64) return fail(c, LBM_ERR_ARG, "single pass needs FP32 arithmetic");
-  if (single_pass && c->P.q == 15) return fail(c, LBM_ERR_ARG, "the single-pass variants are D3Q19 kernels");
+  if (single_pass && single_pass != 5 && c->P.q == 15)
+    return fail(c, LBM_ERR_ARG, "the single-pass variants other than the work list are D3Q19 kernels");
   if (single_pass == 2 && !lbm::onepass_tma_supported(c->P, c->precision))
     return fail(c, LBM_ERR_ARG, "bulk-copy single pass needs FP32 storage, Nx % 4 == 0 and Nx >= 40");
   if (single_pass == 3 && !lbm::onchip_supported(c->P, c->precision))

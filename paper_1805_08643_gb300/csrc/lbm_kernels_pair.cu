@@ -17,6 +17,7 @@
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 #include "lbm_pair.cuh"
+#include "lbm_pair15.cuh"
 #include "lbm_q15.cuh"
 
 namespace lbm {
@@ -87,75 +88,7 @@ __global__ void __launch_bounds__(128) fused_pair_kernel(const S *__restrict__ g
 }
 
 // ------------------------------------------------------------------ D3Q15
-// The same two-node scheme for the D3Q15 variant (lbm_q15.cuh): populations
-// with e_x = 0 as one aligned pair, the others as two scalars; FP16 storage
-// scaled by the D3Q15 weights.
-template <typename S> struct PairIO15 {
-  static __device__ __forceinline__ V2 decode(float2 v, int a) { return PairIO<S>::decode(v, a); }
-  static __device__ __forceinline__ void st2(S *p, int a, V2 v) { PairIO<S>::st2(p, a, v); }
-};
-template <> struct PairIO15<__half> {
-  static __device__ __forceinline__ V2 decode(float2 v, int a) { return V2(v) * V2(q15::w(a)); }
-  static __device__ __forceinline__ void st2(__half *p, int a, V2 v) {
-    *(__half2 *)p = __float22half2_rn(V2(v * V2((double)q15::inv_w(a))).v);
-  }
-};
-
-// Row offset (y', z' part) of the pull source of direction a (x - e_a).
-__device__ __forceinline__ int src_row15(const Nbhd &nb, int a) {
-  switch (a) {
-    case 0: case 1: case 2: return nb.r00;
-    case 3: return nb.rm0;
-    case 4: return nb.rp0;
-    case 5: return nb.r0m;
-    case 6: return nb.r0p;
-    case 7: case 13: return nb.rmm;
-    case 8: case 14: return nb.rpp;
-    case 9: case 12: return nb.rmp;
-    default: return nb.rpm;
-  }
-}
-
-template <typename S>
-__device__ __forceinline__ void pull_pair15(const S *__restrict__ g, unsigned n, const Nbhd &nb, const PairX &px,
-                                            V2 f[q15::kQ]) {
-#pragma unroll
-  for (int a = 0; a < q15::kQ; ++a) {
-    const S *rowp = g + (size_t)a * n + src_row15(nb, a);
-    float2 v;
-    if (q15::ex(a) == 0)
-      v = PairIO<S>::ld2(rowp + px.x);
-    else if (q15::ex(a) > 0)
-      v = make_float2(PairIO<S>::ld1(rowp + px.xm1), PairIO<S>::ld1(rowp + px.x));
-    else
-      v = make_float2(PairIO<S>::ld1(rowp + px.x + 1), PairIO<S>::ld1(rowp + px.xp2));
-    f[a] = PairIO15<S>::decode(v, a);
-  }
-}
-
-// psi(x + e_a) of both nodes, p[a] (Eq. 15 stencil on D3Q15).
-__device__ __forceinline__ void gather_psi_pair15(const float *__restrict__ psi, const Nbhd &nb, const PairX &px,
-                                                  V2 p[q15::kQ]) {
-  // centre pair, and the pairs shifted by +1 and -1 in x
-  auto row3 = [&](int row, V2 &c, V2 &plus, V2 &minus) {
-    const float2 m = __ldg((const float2 *)(psi + row + px.x));
-    const float l = __ldg(psi + row + px.xm1), r = __ldg(psi + row + px.xp2);
-    c = V2(m);
-    plus = V2(m.y, r);
-    minus = V2(l, m.x);
-  };
-  auto row1 = [&](int row) { return V2(__ldg((const float2 *)(psi + row + px.x))); };
-  V2 unused;
-  row3(nb.r00, p[0], p[1], p[2]);
-  p[3] = row1(nb.rp0);
-  p[4] = row1(nb.rm0);
-  p[5] = row1(nb.r0p);
-  p[6] = row1(nb.r0m);
-  row3(nb.rpp, unused, p[7], p[13]);
-  row3(nb.rmm, unused, p[14], p[8]);
-  row3(nb.rpm, unused, p[9], p[12]);
-  row3(nb.rmp, unused, p[11], p[10]);
-}
+// The same two-node scheme for the D3Q15 variant (lbm_pair15.cuh).
 
 template <typename S, int EOS, bool DF>
 __global__ void __launch_bounds__(128) psi_pair15_kernel(const S *__restrict__ g, float *__restrict__ psi,
@@ -177,24 +110,7 @@ __global__ void __launch_bounds__(128) fused_pair15_kernel(const S *__restrict__
   PairX px;
   int y, z;
   if (!pair_of_thread(P, px, y, z)) return;
-  const Nbhd nb(px.x, y, z, P);
-  V2 f[q15::kQ];
-  pull_pair15<S>(g_in, (unsigned)P.n, nb, px, f);
-  V2 Fx, Fy, Fz, dS4;
-  {
-    V2 p[q15::kQ];
-    gather_psi_pair15(psi, nb, px, p);
-    V2 Sx, Sy, Sz;
-    q15::psi_gradient<V2>(p, Sx, Sy, Sz);
-    const V2 kk = V2((double)-P.fG) * p[0];
-    dS4 = SIGMA ? V2(V2((double)P.fsigma_coef) * V2(Sx * Sx + Sy * Sy + Sz * Sz)) : V2(0.0);
-    Fx = kk * Sx;
-    Fy = kk * Sy;
-    Fz = kk * Sz;
-  }
-  q15::collide<V2>(f, V2((double)P.frho_ref), Fx, Fy, Fz, dS4, Rates<V2>(P));
-#pragma unroll
-  for (int a = 0; a < q15::kQ; ++a) PairIO15<S>::st2(g_out + (size_t)a * P.n + nb.self, a, f[a]);
+  fused_pair15_at<S, SIGMA>(g_in, g_out, psi, P, px.x, y, z);
 }
 
 dim3 pair_grid(const KParams &P, const Launch &L) {

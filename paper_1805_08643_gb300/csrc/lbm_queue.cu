@@ -41,6 +41,7 @@
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 #include "lbm_pair.cuh"
+#include "lbm_pair15.cuh"
 
 namespace lbm {
 namespace {
@@ -62,8 +63,9 @@ __host__ __device__ inline TileGeo tile_geo(const KParams &P) {
   return g;
 }
 
-// item: x = fused plane (or -1), y = its tile, z = psi plane (or -1), w = its tile
-template <typename S, int OP, bool SIGMA, int EOS, bool DF>
+// item: x = fused plane (or -1), y = its tile, z = psi plane (or -1), w = its tile.
+// Q: 19 (both operators) or 15 (the D3Q15 non-orthogonal variant).
+template <typename S, int OP, bool SIGMA, int EOS, bool DF, int Q>
 __global__ void __launch_bounds__(NTH, kMinBlocks)
     queue_kernel(const S *__restrict__ g_in, S *__restrict__ g_out, const float *__restrict__ psi_in,
                  float *__restrict__ psi_out, const KParams P, const int4 *__restrict__ items, int nitems,
@@ -78,7 +80,12 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
       int z = it.x, t = it.y;
       asm volatile("" : "+r"(z), "+r"(t));  // keep the row offsets out of the registers across items
       const int x = (t % G.ntx) * 2 * TXP + 2 * lane, y = (t / G.ntx) * kRows + row;
-      if (x < P.nx && y < P.ny) fused_pair_at<S, OP, SIGMA, false>(g_in, g_out, psi_in, P, x, y, z, Rates<V2>(P));
+      if (x < P.nx && y < P.ny) {
+        if constexpr (Q == 15)
+          fused_pair15_at<S, SIGMA>(g_in, g_out, psi_in, P, x, y, z);
+        else
+          fused_pair_at<S, OP, SIGMA, false>(g_in, g_out, psi_in, P, x, y, z, Rates<V2>(P));
+      }
       __syncthreads();
       if (lane == 0 && row == 0) counter_release_add(done + LBM_IDX(z * G.T + t, P.nz * G.T), 1);
     }
@@ -104,16 +111,21 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
       }
       if (!__all_sync(0xffffffffu, ok)) e |= kErrTimeout;
       const int x = tx * 2 * TXP + 2 * lane, y = ty * kRows + row;
-      if (x < P.nx && y < P.ny) psi_pair_at_l2<S, EOS, DF>(g_out, psi_out, P, x, y, z, e);
+      if (x < P.nx && y < P.ny) {
+        if constexpr (Q == 15)
+          psi_pair15_at_l2<S, EOS, DF>(g_out, psi_out, P, x, y, z, e);
+        else
+          psi_pair_at_l2<S, EOS, DF>(g_out, psi_out, P, x, y, z, e);
+      }
     }
   }
   if (e) atomicOr(err, e);
 }
 
-template <typename S, int OP, bool SIGMA, int EOS, bool DF>
+template <typename S, int OP, bool SIGMA, int EOS, bool DF, int Q>
 cudaError_t launch_kernel(const KParams &P, const void *g_in, void *g_out, const void *psi_in, void *psi_out,
                           const QueueState &q, int stamp, unsigned *err, cudaStream_t s) {
-  auto kern = queue_kernel<S, OP, SIGMA, EOS, DF>;
+  auto kern = queue_kernel<S, OP, SIGMA, EOS, DF, Q>;
   const S *gi = (const S *)g_in;
   S *go = (S *)g_out;
   const float *pi = (const float *)psi_in;
@@ -126,24 +138,27 @@ cudaError_t launch_kernel(const KParams &P, const void *g_in, void *g_out, const
   return cudaLaunchCooperativeKernel((const void *)kern, dim3(q.grid), dim3(TXP, kRows), args, 0, s);
 }
 
-template <typename S, int OP, bool SIGMA>
+template <typename S, int OP, bool SIGMA, int Q = 19>
 cudaError_t by_eos(const KParams &P, bool df, const void *g_in, void *g_out, const void *psi_in, void *psi_out,
                    const QueueState &q, int stamp, unsigned *err, cudaStream_t s) {
   switch (P.eos) {
     case kEosCS:
-      return df ? launch_kernel<S, OP, SIGMA, kEosCS, true>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s)
-                : launch_kernel<S, OP, SIGMA, kEosCS, false>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
+      return df ? launch_kernel<S, OP, SIGMA, kEosCS, true, Q>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s)
+                : launch_kernel<S, OP, SIGMA, kEosCS, false, Q>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
     case kEosExp:
-      return df ? launch_kernel<S, OP, SIGMA, kEosExp, true>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s)
-                : launch_kernel<S, OP, SIGMA, kEosExp, false>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
+      return df ? launch_kernel<S, OP, SIGMA, kEosExp, true, Q>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s)
+                : launch_kernel<S, OP, SIGMA, kEosExp, false, Q>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
     default:
-      return launch_kernel<S, OP, SIGMA, kEosNone, false>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
+      return launch_kernel<S, OP, SIGMA, kEosNone, false, Q>(P, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
   }
 }
 
 template <typename S>
 cudaError_t by_op(const KParams &P, int op, bool sigma, bool df, const void *g_in, void *g_out, const void *psi_in,
                   void *psi_out, const QueueState &q, int stamp, unsigned *err, cudaStream_t s) {
+  if (P.q == 15)
+    return sigma ? by_eos<S, kNonOrth, true, 15>(P, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s)
+                 : by_eos<S, kNonOrth, false, 15>(P, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
   if (op == kNonOrth)
     return sigma ? by_eos<S, kNonOrth, true>(P, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s)
                  : by_eos<S, kNonOrth, false>(P, df, g_in, g_out, psi_in, psi_out, q, stamp, err, s);
@@ -157,8 +172,9 @@ cudaError_t by_op(const KParams &P, int op, bool sigma, bool df, const void *g_i
 template <typename S>
 cudaError_t occupancy_of(int *per_sm) {
   using K = void (*)(const S *, S *, const float *, float *, const KParams, const int4 *, int, int *, int, unsigned *);
-  const K ks[] = {queue_kernel<S, kNonOrth, true, kEosCS, false>, queue_kernel<S, kOrth, true, kEosCS, false>,
-                  queue_kernel<S, kNonOrth, false, kEosCS, true>, queue_kernel<S, kOrth, false, kEosExp, false>};
+  const K ks[] = {queue_kernel<S, kNonOrth, true, kEosCS, false, 19>, queue_kernel<S, kOrth, true, kEosCS, false, 19>,
+                  queue_kernel<S, kNonOrth, false, kEosCS, true, 19>, queue_kernel<S, kOrth, false, kEosExp, false, 19>,
+                  queue_kernel<S, kNonOrth, true, kEosCS, false, 15>, queue_kernel<S, kNonOrth, false, kEosExp, true, 15>};
   int m = 1 << 30;
   for (K k : ks) {
     int v = 0;
@@ -325,7 +341,7 @@ bool place_psi_jobs(std::vector<int4> &out, const std::vector<long long> &ready,
 
 }  // namespace
 
-bool queue_supported(const KParams &P, int precision) { return precision != kF64 && P.nx % 2 == 0 && P.q == 19; }
+bool queue_supported(const KParams &P, int precision) { return precision != kF64 && P.nx % 2 == 0; }
 
 cudaError_t queue_grid(int precision, int *grid) {
   int per_sm = 0, dev = 0, sms = 0;

@@ -267,8 +267,9 @@ class Lattice:
     def set_tuning(self, single_pass=True, tile=1, z_planes=0):
         """single_pass: False / True (register-prefetch kernel) / "tma" (bulk-copy kernel) /
         "onchip" (psi evaluated on chip by producer warps; Nx even) / "lagged" (the next psi pass one plane
-        behind the fused pass in one cooperative launch; Nx even) / "queue" (fused and next-psi items of
-        row bands from an ordered work queue in one persistent launch; Nx even, D3Q19)."""
+        behind the fused pass in one cooperative launch; Nx even) / "queue" (fused and next-psi tile jobs from
+        an ordered work list in one cooperative launch; Nx even; the only single pass of a D3Q15 box and the
+        default with FP32 storage)."""
         if isinstance(single_pass, str):
             modes = {"tma": 2, "onchip": 3, "lagged": 4, "queue": 5}
             if single_pass not in modes:

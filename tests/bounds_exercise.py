@@ -83,6 +83,9 @@ def main():
                 run_box(grid, op, "f32", mode, out)
             for mode in (True, "queue"):
                 run_box(grid, op, "f16", mode, out)
+        for prec in ("f32", "f16"):
+            run_box(grid, "nonorth_d3q15", prec, "queue", out)
+            run_box(grid, "nonorth_d3q15", prec, False, out)
     run_box((5, 4, 4), "nonorth", "f32", None, out)  # odd Nx: one-node kernels
     run_box((5, 4, 4), "orth", "f32", True, out)
     for prec in ("f32", "f16"):

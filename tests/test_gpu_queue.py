@@ -160,12 +160,44 @@ def test_queue_at_256_cubed_equals_two_pass():
 
 
 def test_default_step_per_form():
-    """FP32 storage on D3Q19 with an even Nx steps on the work list by default; FP16 storage, FP64, an odd
-    Nx and D3Q15 keep the two-pass step."""
+    """FP32 storage with an even Nx steps on the work list by default (D3Q19 and D3Q15); FP16 storage, FP64
+    and an odd Nx keep the two-pass step."""
     cases = [((16, 16, 16), "nonorth", "f32", "queue"), ((16, 16, 16), "orth", "f32", "queue"),
              ((16, 16, 16), "nonorth", "f16", False), ((16, 16, 16), "nonorth", "f64", False),
-             ((15, 16, 16), "nonorth", "f32", False), ((16, 16, 16), "nonorth_d3q15", "f32", False)]
+             ((15, 16, 16), "nonorth", "f32", False), ((16, 16, 16), "nonorth_d3q15", "f32", "queue"),
+             ((16, 16, 16), "nonorth_d3q15", "f16", False)]
     for grid, op, prec, want in cases:
         lat = lattice(grid, op, prec, physics())
         assert lat.tuning()["single_pass"] == want, (grid, op, prec)
         lat.close()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("grid", [(32, 32, 32), (24, 20, 28), (6, 5, 7)])
+def test_d3q15_work_list_equals_two_pass_bit_for_bit(grid, prec):
+    """The D3Q15 variant on the work list (its own fused and psi tile jobs) against its two-pass kernels."""
+    steps = 30
+    s0, ref = _run(grid, "nonorth_d3q15", prec, False, steps, sigma=0.105)
+    s1, got = _run(grid, "nonorth_d3q15", prec, "queue", steps, sigma=0.105)
+    assert s0 == 0 and s1 == 0
+    assert _equal(ref, got)
+
+
+def test_d3q15_work_list_against_its_oracle():
+    from oracle import d3q15 as D
+
+    grid, steps = (24, 20, 28), 200
+    phys = physics(rates=SIX_RATES)
+    rl, rv = coexistence(0.8)
+    centre = tuple(n / 2 for n in grid)
+    lat = lattice(grid, "nonorth_d3q15", "f32", phys)
+    lat.set_tuning("queue", 1, 0)
+    lat.init_droplet(centre, 6.0, 2.0, rl, rv)
+    lat.step(steps)
+    assert lat.check() == 0
+    rho, u = lat.moments()
+    lat.close()
+    p = oracle_params(grid, "nonorth", phys)
+    f0 = D.equilibrium_state(p, droplet_rho(grid, centre, 6.0, 2.0, rl, rv))
+    rho_o, u_o, _, _ = D.macroscopic(p, D.run(p, f0, steps))
+    assert max_abs(rho, rho_o) <= 2e-5 and max_abs(u, u_o) <= 2e-5
