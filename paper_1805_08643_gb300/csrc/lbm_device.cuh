@@ -148,11 +148,39 @@ __device__ __forceinline__ PsiT eos_psi(double rho, float rho_f, const KParams &
   return (PsiT)(xf * rsqrtf(xf * (one_m * one_m * one_m)));
 }
 
+// FP32 -> FP64 widening and FP64 -> FP32 rounding (to nearest, ties to even)
+// done on the integer units: GB300 issues two FP64 instructions per SM and
+// clock, conversions included, and the EOS below is bound by that rate, while
+// the integer units are idle.  Both are exact bit manipulations of IEEE 754
+// binary32 / binary64 (bias 127 / 1023, 23 / 52 fraction bits), so the results
+// equal the conversion instructions'; values outside the range handled (zero
+// and subnormal inputs, results outside the normal FP32 range) take the
+// conversion instruction.
+__device__ __forceinline__ double widen_f32(float v) {
+  const unsigned u = __float_as_uint(v), ex = u & 0x7f800000u;
+  if (ex == 0x7f800000u || (ex == 0u && (u << 1) != 0u)) return (double)v;  // inf, nan, subnormal
+  // sign, exponent + (1023 - 127), top 20 fraction bits; the last 3 fraction bits open the low word (a zero
+  // keeps its sign and nothing else)
+  const unsigned hi = ex ? (u & 0x80000000u) | (((u >> 3) & 0x0fffffffu) + 0x38000000u) : (u & 0x80000000u);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+__device__ __forceinline__ float narrow_f64(double v) {
+  const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+  const unsigned E = (hi >> 20) & 0x7ffu;
+  if (E < 897u || E > 1150u) return (float)v;  // FP32 exponent E - 896 outside 1..254
+  // sign, E - 896, the top 23 of the 52 fraction bits; then round on the 29 dropped bits
+  unsigned r = (hi & 0x80000000u) | (((hi & 0x7fffffffu) - (896u << 20)) << 3) | (lo >> 29);
+  const unsigned rem = lo & 0x1fffffffu;
+  r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;  // a carry moves into the exponent
+  return __uint_as_float(r);
+}
+
 // psi in FP32 from d = rho - rho_ref (the FP32-arithmetic forms): the radicand
 // X as a quintic in d, Horner in FP64 from host-made coefficients (KParams::c),
 // five FMA and no separate rho_ref + d, one FP64 operation fewer than the
 // quintic in rho; checks and the final root as in eos_psi's FP32-psi path.
-template <int EOS>
+template <int EOS, bool ICVT = true>
 __device__ __forceinline__ float eos_psi_d(float d, const KParams &P, unsigned &err) {
   const float nan = __int_as_float(0x7fc00000);
   if (EOS == kEosNone) return 0.f;
@@ -161,9 +189,9 @@ __device__ __forceinline__ float eos_psi_d(float d, const KParams &P, unsigned &
   if (!(rho_f > 0.0f)) { err |= kErrEosDomain; return nan; }
   if (EOS == kEosExp) return (float)(P.psi0 * exp(-P.rho0 / (P.rho_ref + (double)d)));
   if (!(rho_f < P.f_rho_max)) { err |= kErrEosDomain; return nan; }
-  const double x = (double)d;
+  const double x = ICVT ? widen_f32(d) : (double)d;
   const double X = fma(fma(fma(fma(fma(P.c[5], x, P.c[4]), x, P.c[3]), x, P.c[2]), x, P.c[1]), x, P.c[0]);
-  const float xf = (float)X;
+  const float xf = ICVT ? narrow_f64(X) : (float)X;
   if (!(xf >= 0.0f)) { err |= kErrEosDomain; return nan; }
   if (xf == 0.0f) return 0.f;
   const float one_m = fmaf(-P.fb4, rho_f, 1.0f);

@@ -80,7 +80,7 @@ __device__ __forceinline__ V2 drho_pair(const V2 f[19]) {
 }
 
 // psi of both nodes from rho - rho_ref; DF selects the compensated-FP32 radicand.
-template <int EOS, bool DF>
+template <int EOS, bool DF, bool ICVT = true>
 __device__ __forceinline__ float2 psi_pair(V2 drho, const KParams &P, unsigned &e) {
   float out[2];
 #pragma unroll
@@ -89,7 +89,7 @@ __device__ __forceinline__ float2 psi_pair(V2 drho, const KParams &P, unsigned &
     if (DF)
       out[k] = eos_psi_f2<EOS>(d, P, e);
     else
-      out[k] = eos_psi_d<EOS>(d, P, e);
+      out[k] = eos_psi_d<EOS, ICVT>(d, P, e);
   }
   return make_float2(out[0], out[1]);
 }
@@ -189,7 +189,7 @@ __device__ __forceinline__ void fused_pair_at(const S *__restrict__ g_in, S *__r
 
 // psi of one pair from populations written earlier in the same launch (the
 // psi pass of psi_pair_kernel, pulls through L2).
-template <typename S, int EOS, bool DF>
+template <typename S, int EOS, bool DF, bool ICVT = true>
 __device__ __forceinline__ void psi_pair_at_l2(const S *__restrict__ g, float *__restrict__ psi, const KParams &P,
                                                int x, int y, int z, unsigned &e) {
   const PairX px = pair_x(P, x);
@@ -207,7 +207,7 @@ __device__ __forceinline__ void psi_pair_at_l2(const S *__restrict__ g, float *_
       v = make_float2(L2Load<S>::ld1(rowp + px.x + 1), L2Load<S>::ld1(rowp + px.xp2));
     f[a] = PairIO<S>::decode(v, a);
   }
-  *(float2 *)(psi + nb.self) = psi_pair<EOS, DF>(drho_pair(f), P, e);
+  *(float2 *)(psi + nb.self) = psi_pair<EOS, DF, ICVT>(drho_pair(f), P, e);
 }
 
 // Cross-block signalling inside one launch: a release increment of a

@@ -108,14 +108,14 @@ __device__ __forceinline__ void fused_pair15_at(const S *__restrict__ g_in, S *_
 }
 
 // psi of one pair on D3Q15 from populations written earlier in the same launch (pulls through L2).
-template <typename S, int EOS, bool DF>
+template <typename S, int EOS, bool DF, bool ICVT = true>
 __device__ __forceinline__ void psi_pair15_at_l2(const S *__restrict__ g, float *__restrict__ psi, const KParams &P,
                                                  int x, int y, int z, unsigned &e) {
   const PairX px = pair_x(P, x);
   const Nbhd nb(x, y, z, P);
   V2 f[q15::kQ];
   pull_pair15<S, L2Load<S>>(g, (unsigned)P.n, nb, px, f);
-  *(float2 *)(psi + nb.self) = psi_pair<EOS, DF>(q15::drho(f), P, e);
+  *(float2 *)(psi + nb.self) = psi_pair<EOS, DF, ICVT>(q15::drho(f), P, e);
 }
 
 }  // namespace lbm

@@ -50,6 +50,11 @@ constexpr int TXP = 32;          // pair columns of a tile: 64 nodes
 constexpr int kRows = 4;         // rows of a tile (one warp each)
 constexpr int NTH = TXP * kRows;
 constexpr int kMinBlocks = 6;    // resident blocks per SM the register budget is set for
+// The psi jobs convert to and from FP64 with the conversion instructions, not
+// the integer path of the psi pass kernel (the same results): this kernel is
+// not bound by the FP64 unit, and the integer work cost 1 % (FP32 storage) and
+// 3 % (FP16) of a 256^3 step on GB300.
+constexpr bool kIntCvt = false;
 
 struct TileGeo {
   int ntx, nty, T;  // tiles along x, along y, per plane
@@ -113,9 +118,9 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
       const int x = tx * 2 * TXP + 2 * lane, y = ty * kRows + row;
       if (x < P.nx && y < P.ny) {
         if constexpr (Q == 15)
-          psi_pair15_at_l2<S, EOS, DF>(g_out, psi_out, P, x, y, z, e);
+          psi_pair15_at_l2<S, EOS, DF, kIntCvt>(g_out, psi_out, P, x, y, z, e);
         else
-          psi_pair_at_l2<S, EOS, DF>(g_out, psi_out, P, x, y, z, e);
+          psi_pair_at_l2<S, EOS, DF, kIntCvt>(g_out, psi_out, P, x, y, z, e);
       }
     }
   }
@@ -292,7 +297,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
       if (!__all_sync(0xffffffffu, ok)) e |= kErrTimeout;
       const int in = B.cur ^ parity, half = G.tw / 2;
       const int x = tx * G.tw + 2 * (tid % half), y = ty * G.th + tid / half;
-      if (x < P.nx && y < P.ny) psi_pair_at_l2<S, EOS, false>((const S *)B.g[in ^ 1], B.psi[in ^ 1], P, x, y, z, e);
+      if (x < P.nx && y < P.ny) psi_pair_at_l2<S, EOS, false, kIntCvt>((const S *)B.g[in ^ 1], B.psi[in ^ 1], P, x, y, z, e);
     }
     it = next;
   }
