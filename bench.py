@@ -288,8 +288,9 @@ def e2e_run(op, prec, edge, steps):
 
 
 def batched_run(steps, warmup, n_boxes=512):
-    """The batched workload: n_boxes periodic boxes (edges 32/48/64/96); every edge is even, so each step is
-    the fused pass and the psi pass of the pair kernels over the work-item table (two launches)."""
+    """The batched workload: n_boxes periodic boxes (edges 32/48/64/96, every edge even), stepped as the
+    autotuner picks: the work list (one launch per step) or the two-pass pair kernels (a flat fused grid per
+    operator, then the psi pass over work items: three launches per step)."""
     import torch
 
     from paper_1805_08643_gb300 import synth, thermo, tune

@@ -312,16 +312,19 @@ lbm_status lbm_batch_init_droplet(lbm_batch *b, int id, const double centre[3], 
 lbm_status lbm_batch_init_flat(lbm_batch *b, int id, int axis, double lo, double hi, double W, double rho_l,
                                double rho_v);
 
-/* Step of the batch: 3 (the default) the work-list single pass when every box
- * has an even Nx (one cooperative launch per step over 64x4 tile jobs of all
- * boxes: fused jobs and the next step's psi jobs, each box's psi jobs half a
- * wave of the grid behind the fused jobs they read; its completion counters,
- * 4 bytes per tile and plane, are cleared by a memset in the step graph); 0, 1,
- * 2 the tile shape (32x4, 32x8, 64x4) of the two-pass pair kernels, or of the
- * one-node single pass that any batch with an odd-Nx box runs; and, for box id
- * >= 0, its z planes per work item of those (0 = automatic).  Results do not
- * depend on the choice (the work list and the two-pass kernels are equal bit
- * for bit). */
+/* Step of the batch's boxes with an even Nx: 3 (the default) the work-list
+ * single pass (one cooperative launch per step over tile jobs of all boxes:
+ * fused jobs and the next step's psi jobs, each box's psi jobs half a wave of
+ * the grid behind the fused jobs they read; its completion counters, 4 bytes
+ * per tile and plane, are cleared by a memset in the step graph); 0, 1, 2 the
+ * two-pass pair kernels with that tile shape (32x4, 32x8, 64x4): the fused pass
+ * as a flat grid of one block per plane of a tile, one launch per operator (a
+ * block-to-box table of 4 bytes per block), then the psi pass over work items
+ * of a tile through z planes.  Boxes with an odd Nx run the one-node single
+ * pass in the same step, tile shape as chosen (32x8 under 3).  For box id >= 0,
+ * z_planes sets its planes per work item of the psi pass and the single pass
+ * (0 = automatic).  Results do not depend on the choice (the work list and the
+ * two-pass kernels are equal bit for bit). */
 lbm_status lbm_batch_set_tuning(lbm_batch *b, int tile, int id, int z_planes);
 
 /* Advance every initialised box n >= 1 steps (even n replays the two-step graph

@@ -1,8 +1,9 @@
-// Batched boxes: many independent periodic boxes advanced together by
-// persistent launches over a table of work items, the launches of two steps
-// captured in a CUDA graph.  When every box has an even Nx a step is the
-// two-pass pair kernels (fused pass, then psi of the new level); otherwise it
-// is one single-pass launch.  Boxes can join and leave
+// Batched boxes: many independent periodic boxes advanced together, the
+// launches of two steps captured in a CUDA graph.  Boxes with an even Nx step
+// on the work list (one cooperative launch) or on the two-pass pair kernels
+// (the fused pass as a flat grid per operator, then psi of the new level over
+// work items); boxes with an odd Nx on the one-node single pass, in the same
+// step graph.  Boxes can join and leave
 // between calls (continuous batching); each box's buffers come from the
 // stream-ordered allocator and count against the batch's HBM budget.
 #include <cuda_runtime.h>
@@ -65,6 +66,9 @@ struct lbm_batch {
   bool wl = false;           // ... or the work-list single pass
   bool odd = false;          // ... and the one-node single pass for the odd-Nx boxes
   int *d_done = nullptr;     // its completion counters, cleared before every launch
+  int *d_fmap = nullptr;     // two-pass step: the box of every block of the flat fused grids
+  long long cap_fmap = 0;
+  int fused_blocks[2] = {0, 0};  // ... non-orthogonal boxes' blocks, then orthogonal
   long long cap_done = 0, ndone = 0;
   int wl_grid = 0;
   // graphs of two steps and of one step, for each starting parity: the state of
@@ -190,6 +194,34 @@ lbm_status rebuild(lbm_batch *b) {
     b->ndone = nc;
   } else {
     tile_items(even);
+    // the flat fused grids: one block per plane of a tile, non-orthogonal boxes first, box by box
+    int bx, by;
+    lbm::onepass_tile_shape(tile, &bx, &by);
+    std::vector<int> fmap;
+    for (int g = 0; g < 2; ++g) {
+      const int op = g == 0 ? lbm::kNonOrth : lbm::kOrth;
+      const size_t before = fmap.size();
+      for (auto &o : even) {
+        BatchBox &d = b->boxes[o.second].d;
+        if (d.op != op) continue;
+        const long long T = (long long)((d.P.nx + bx - 1) / bx) * ((d.P.ny + by - 1) / by);
+        if ((long long)fmap.size() + T * d.P.nz > (1LL << 31) - 1) return bfail(b, LBM_ERR_ARG, "batch too large");
+        d.qbase = (int)fmap.size();
+        desc[o.second].qbase = d.qbase;
+        fmap.insert(fmap.end(), (size_t)(T * d.P.nz), o.second);
+      }
+      b->fused_blocks[g] = (int)(fmap.size() - before);
+    }
+    if ((long long)fmap.size() > b->cap_fmap) {
+      if (b->d_fmap) cudaFreeAsync(b->d_fmap, b->stream);
+      b->d_fmap = nullptr;
+      BCK(cudaMallocAsync((void **)&b->d_fmap, sizeof(int) * fmap.size(), b->stream), "fused block map");
+      b->cap_fmap = (long long)fmap.size();
+    }
+    if (!fmap.empty())
+      BCK(cudaMemcpyAsync(b->d_fmap, fmap.data(), sizeof(int) * fmap.size(), cudaMemcpyHostToDevice, b->stream),
+          "H2D fused block map");
+    BCK(cudaStreamSynchronize(b->stream), "sync");  // fmap goes out of scope
   }
   const int n_even = (int)items.size();
   tile_items(odd);
@@ -223,8 +255,8 @@ lbm_status rebuild(lbm_batch *b) {
           e = lbm::launch_batch_queue(b->precision, b->eos, b->d_boxes, b->d_items, n_even, parity, b->wl_grid,
                                       b->d_done, (int)b->ndone, b->d_err, b->stream);
       } else if (n_even) {
-        e = lbm::launch_batch_pair(b->precision, b->eos, tile, b->d_boxes, b->d_items, n_even, parity,
-                                   b->grid_blocks, pair_per_sm, b->d_err, b->stream);
+        e = lbm::launch_batch_pair(b->precision, b->eos, tile, b->d_boxes, b->d_items, n_even, b->d_fmap,
+                                   b->fused_blocks, parity, b->grid_blocks, pair_per_sm, b->d_err, b->stream);
       }
       if (e == cudaSuccess && n_odd)
         e = lbm::launch_batch_onepass(b->precision, b->eos, tile, b->d_boxes, b->d_items + n_even, n_odd, parity,
@@ -538,6 +570,7 @@ void lbm_batch_destroy(lbm_batch *b) {
   if (b->d_items) cudaFreeAsync(b->d_items, b->stream);
   if (b->d_red) cudaFreeAsync(b->d_red, b->stream);
   if (b->d_done) cudaFreeAsync(b->d_done, b->stream);
+  if (b->d_fmap) cudaFreeAsync(b->d_fmap, b->stream);
   if (b->d_err) cudaFreeAsync(b->d_err, b->stream);
   if (b->d_scratch) cudaFreeAsync(b->d_scratch, b->stream);
   cudaStreamSynchronize(b->stream);

@@ -145,20 +145,26 @@ struct alignas(16) BatchBox {  // 16-byte aligned: copied to shared memory in 16
   float *psi[2];
   int op;
   int cur;
-  int qbase;  // first completion counter of this box in the batch work list
+  int qbase;  // first completion counter of this box in the batch work list, or (two-pass step) its first
+              // block of the flat fused grid
   int tw;     // its tile width there (batch_tile_width)
 };
 
 // Persistent single-pass launch over the work items (box, tx | ty << 16, z0, z1)
 // of many boxes; grid = number of thread blocks.  FP32 arithmetic forms only.
 // The batch's two-pass step on the pair kernels (every box with an even Nx):
-// the fused pass, then the psi pass of the new level, for one parity.  Each is
-// a persistent grid of sms x per_sm[k] blocks (at most one per item), per_sm
-// as batch_pair_occupancy gives it: resident blocks per SM of the fused (0)
-// and psi (1) kernels.
+// the fused pass, then the psi pass of the new level, for one parity.  The
+// fused pass is a flat grid per operator, one block per plane of a tile of the
+// chosen shape: block_box holds the box of every block, the non-orthogonal
+// boxes' fused_blocks[0] blocks first, then the orthogonal boxes'
+// fused_blocks[1]; a box's blocks are consecutive from its descriptor's qbase,
+// plane by plane, tiles x-fastest.  The psi pass is a persistent grid of
+// sms x per_sm[1] blocks over the items (at most one per item), per_sm as
+// batch_pair_occupancy gives it (resident blocks per SM; [0] is unused).
 cudaError_t batch_pair_occupancy(int precision, int eos, int tile, int per_sm[2]);
 cudaError_t launch_batch_pair(int precision, int eos, int tile, const BatchBox *boxes, const int4 *items, int nitems,
-                              int parity, int sms, const int per_sm[2], unsigned *err, cudaStream_t s);
+                              const int *block_box, const int fused_blocks[2], int parity, int sms,
+                              const int per_sm[2], unsigned *err, cudaStream_t s);
 cudaError_t launch_batch_onepass(int precision, int eos, int tile, const BatchBox *boxes, const int4 *items,
                                  int nitems, int parity, int grid, unsigned *err, cudaStream_t s);
 // Block shape of a tile choice: returns threads per block, sets bx, by.

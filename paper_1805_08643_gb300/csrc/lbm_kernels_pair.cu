@@ -158,15 +158,17 @@ cudaError_t fused_pair_dispatch(const KParams &P, int op, bool sigma, const void
   return cudaGetLastError();
 }
 
-// Batched boxes, two-pass step: work item w = (box, tile_x | tile_y << 16, z0, z1)
-// is a TXP x TY tile of pairs (2 TXP x TY nodes) of one box through planes
-// [z0, z1).  The fused pass reads level in = cur ^ parity (populations and psi)
-// and writes the populations of level in ^ 1; the psi pass then evaluates psi
-// of level in ^ 1, so after a step psi of the current level is always valid.
-template <typename S, bool PSI, int EOS, int TXP, int TY>
-__global__ void __launch_bounds__(TXP *TY) batch_pair_kernel(const BatchBox *__restrict__ boxes,
-                                                             const int4 *__restrict__ items, int nitems, int parity,
-                                                             unsigned *__restrict__ err) {
+// Batched boxes, two-pass step, psi pass: work item w = (box, tile_x | tile_y
+// << 16, z0, z1) is a TXP x TY tile of pairs (2 TXP x TY nodes) of one box
+// through planes [z0, z1).  The fused pass (batch_flat_fused_kernel) reads
+// level in = cur ^ parity (populations and psi) and writes the populations of
+// level in ^ 1; this pass then evaluates psi of level in ^ 1, so after a step
+// psi of the current level is always valid.  (A flat grid of one plane per
+// block, as for the fused pass, measured 2 % slower here.)
+template <typename S, int EOS, int TXP, int TY>
+__global__ void __launch_bounds__(TXP *TY) batch_psi_kernel(const BatchBox *__restrict__ boxes,
+                                                            const int4 *__restrict__ items, int nitems, int parity,
+                                                            unsigned *__restrict__ err) {
   __shared__ BatchBox bb;
   const int tid = threadIdx.y * TXP + threadIdx.x;
   unsigned e = 0;
@@ -184,75 +186,101 @@ __global__ void __launch_bounds__(TXP *TY) batch_pair_kernel(const BatchBox *__r
     const int x = (w.y & 0xffff) * (2 * TXP) + 2 * threadIdx.x, y = (w.y >> 16) * TY + threadIdx.y;
     if (x >= P.nx || y >= P.ny) continue;
     const PairX px{x, x == 0 ? P.nx - 1 : x - 1, x + 2 >= P.nx ? x + 2 - P.nx : x + 2};
-    if (PSI) {
-      const S *g = (const S *)bb.g[in ^ 1];
-      float *psi = bb.psi[in ^ 1];
-      for (int z = w.z; z < w.w; ++z) {
-        const Nbhd nb(x, y, z, P);
-        V2 f[19];
-        pull_pair<S>(g, (unsigned)P.n, nb, px, f);
-        *(float2 *)(psi + nb.self) = psi_pair<EOS, false>(drho_pair(f), P, e);
-      }
-    } else {
-      const S *g_in = (const S *)bb.g[in];
-      S *g_out = (S *)bb.g[in ^ 1];
-      const float *psi = bb.psi[in];
-      const Rates<V2> r(P);
-      for (int z = w.z; z < w.w; ++z) {
-        const Nbhd nb(x, y, z, P);
-        V2 f[19];
-        pull_pair<S>(g_in, (unsigned)P.n, nb, px, f);
-        V2 p[19];
-        gather_psi_pair(psi, nb, px, p);
-        force_collide_pair<2, true>(f, p, P, r, bb.op);
-#pragma unroll
-        for (int a = 0; a < 19; ++a) PairIO<S>::st2(g_out + (size_t)a * P.n + nb.self, a, f[a]);
-      }
+    const S *g = (const S *)bb.g[in ^ 1];
+    float *psi = bb.psi[in ^ 1];
+    for (int z = w.z; z < w.w; ++z) {
+      const Nbhd nb(x, y, z, P);
+      V2 f[19];
+      pull_pair<S>(g, (unsigned)P.n, nb, px, f);
+      *(float2 *)(psi + nb.self) = psi_pair<EOS, false>(drho_pair(f), P, e);
     }
   }
   if (e) atomicOr(err, e);
 }
 
+// Threads per SM the flat fused kernel's registers are set for: 640 (at most 102 registers a thread; both
+// operators fit without spilling, the orthogonal one took 108 unbounded; 80 registers spilled and was slower).
+constexpr int kFlatFusedThreadsPerSM = 640;
+
+// The fused pass of a batch as a flat grid, one launch per operator: block b
+// is one plane of one 2 TXP x TY tile of one box, block_box[offset + b] names
+// the box, whose first block is its descriptor's qbase; planes are numbered
+// box by box, tiles x-fastest within a plane.  One node pair per thread and no
+// loop, as in fused_pair_kernel: a persistent kernel looping over the planes of
+// an item held 128 registers (16 warps per SM) and reached 0.86 of the copy
+// bandwidth, this one holds 96 (5 blocks of 128 threads) and 0.94.
+template <typename S, int OP, int TXP, int TY>
+__global__ void __launch_bounds__(TXP *TY, kFlatFusedThreadsPerSM / (TXP * TY)) batch_flat_fused_kernel(const BatchBox *__restrict__ boxes,
+                                                                   const int *__restrict__ block_box, int offset,
+                                                                   int parity) {
+  const int gb = offset + (int)blockIdx.x;
+  const int slot = __ldg(block_box + gb);
+  const BatchBox &bb = boxes[slot];  // read where used (cached; a copy to shared memory measured the same)
+  const KParams &P = bb.P;
+  const int ntx = (P.nx + 2 * TXP - 1) / (2 * TXP), nty = (P.ny + TY - 1) / TY, T = ntx * nty;
+  const int local = gb - bb.qbase, z = local / T, t = local - z * T;
+  const int x = (t % ntx) * (2 * TXP) + 2 * threadIdx.x, y = (t / ntx) * TY + threadIdx.y;
+  if (x >= P.nx || y >= P.ny || z >= P.nz) return;
+  const int in = bb.cur ^ parity;
+  fused_pair_at<S, OP, true, false>((const S *)bb.g[in], (S *)bb.g[in ^ 1], bb.psi[in], P, x, y, z, Rates<V2>(P));
+}
+
 // The fused and psi kernels of one step for a storage type and tile shape;
 // with query set, per_sm receives their resident blocks per SM instead.
 template <typename S, int TXP, int TY>
-cudaError_t batch_pair_shape(int eos, const BatchBox *boxes, const int4 *items, int nitems, int parity, int sms,
-                             int per_sm[2], bool query, unsigned *err, cudaStream_t s) {
+cudaError_t batch_pair_shape(int eos, const BatchBox *boxes, const int4 *items, int nitems, const int *block_box,
+                             const int fused_blocks[2], int parity, int sms, int per_sm[2], bool query, unsigned *err,
+                             cudaStream_t s) {
   using K = void (*)(const BatchBox *, const int4 *, int, int, unsigned *);
-  K k[2] = {batch_pair_kernel<S, false, kEosNone, TXP, TY>, nullptr};
+  K kpsi;
   switch (eos) {
-    case kEosCS: k[1] = batch_pair_kernel<S, true, kEosCS, TXP, TY>; break;
-    case kEosExp: k[1] = batch_pair_kernel<S, true, kEosExp, TXP, TY>; break;
-    default: k[1] = batch_pair_kernel<S, true, kEosNone, TXP, TY>; break;
+    case kEosCS: kpsi = batch_psi_kernel<S, kEosCS, TXP, TY>; break;
+    case kEosExp: kpsi = batch_psi_kernel<S, kEosExp, TXP, TY>; break;
+    default: kpsi = batch_psi_kernel<S, kEosNone, TXP, TY>; break;
   }
-  for (int i = 0; i < 2; ++i) {
-    cudaError_t e;
-    if (query) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[i], k[i], TXP * TY, 0);
-    } else {
-      const int grid = std::max(1, std::min(sms * std::max(per_sm[i], 1), nitems));
-      k[i]<<<grid, dim3(TXP, TY), 0, s>>>(boxes, items, nitems, parity, err);
-      e = cudaGetLastError();
-    }
-    if (e != cudaSuccess) return e;
+  if (query) {
+    per_sm[0] = 0;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], kpsi, TXP * TY, 0);
   }
-  return cudaSuccess;
+  // fused pass: the flat launches (non-orthogonal boxes' blocks first in block_box, then the orthogonal ones)
+  if (fused_blocks[0] > 0)
+    batch_flat_fused_kernel<S, kNonOrth, TXP, TY><<<fused_blocks[0], dim3(TXP, TY), 0, s>>>(boxes, block_box, 0, parity);
+  if (fused_blocks[1] > 0)
+    batch_flat_fused_kernel<S, kOrth, TXP, TY><<<fused_blocks[1], dim3(TXP, TY), 0, s>>>(boxes, block_box, fused_blocks[0],
+                                                                                       parity);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(sms * std::max(per_sm[1], 1), nitems));
+  kpsi<<<grid, dim3(TXP, TY), 0, s>>>(boxes, items, nitems, parity, err);
+  return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t batch_pair_tile(int tile, int eos, const BatchBox *boxes, const int4 *items, int nitems, int parity,
-                            int sms, int per_sm[2], bool query, unsigned *err, cudaStream_t s) {
+cudaError_t batch_pair_tile(int tile, int eos, const BatchBox *boxes, const int4 *items, int nitems,
+                            const int *block_box, const int fused_blocks[2], int parity, int sms, int per_sm[2],
+                            bool query, unsigned *err, cudaStream_t s) {
   switch (tile) {
-    case kTile32x4: return batch_pair_shape<S, 16, 4>(eos, boxes, items, nitems, parity, sms, per_sm, query, err, s);
-    case kTile64x4: return batch_pair_shape<S, 32, 4>(eos, boxes, items, nitems, parity, sms, per_sm, query, err, s);
-    default: return batch_pair_shape<S, 16, 8>(eos, boxes, items, nitems, parity, sms, per_sm, query, err, s);
+    case kTile32x4:
+      return batch_pair_shape<S, 16, 4>(eos, boxes, items, nitems, block_box, fused_blocks, parity, sms, per_sm, query,
+                                        err, s);
+    case kTile64x4:
+      return batch_pair_shape<S, 32, 4>(eos, boxes, items, nitems, block_box, fused_blocks, parity, sms, per_sm, query,
+                                        err, s);
+    default:
+      return batch_pair_shape<S, 16, 8>(eos, boxes, items, nitems, block_box, fused_blocks, parity, sms, per_sm, query,
+                                        err, s);
   }
 }
 
 cudaError_t batch_pair_dispatch(int precision, int tile, int eos, const BatchBox *boxes, const int4 *items, int nitems,
-                                int parity, int sms, int per_sm[2], bool query, unsigned *err, cudaStream_t s) {
-  if (precision == kF32) return batch_pair_tile<float>(tile, eos, boxes, items, nitems, parity, sms, per_sm, query, err, s);
-  if (precision == kF16) return batch_pair_tile<__half>(tile, eos, boxes, items, nitems, parity, sms, per_sm, query, err, s);
+                                const int *block_box, const int fused_blocks[2], int parity, int sms, int per_sm[2],
+                                bool query, unsigned *err, cudaStream_t s) {
+  if (precision == kF32)
+    return batch_pair_tile<float>(tile, eos, boxes, items, nitems, block_box, fused_blocks, parity, sms, per_sm, query,
+                                  err, s);
+  if (precision == kF16)
+    return batch_pair_tile<__half>(tile, eos, boxes, items, nitems, block_box, fused_blocks, parity, sms, per_sm,
+                                   query, err, s);
   return cudaErrorInvalidValue;
 }
 
@@ -261,13 +289,16 @@ cudaError_t batch_pair_dispatch(int precision, int tile, int eos, const BatchBox
 bool pair_supported(const KParams &P, int precision) { return precision != kF64 && P.nx % 2 == 0; }
 
 cudaError_t batch_pair_occupancy(int precision, int eos, int tile, int per_sm[2]) {
-  return batch_pair_dispatch(precision, tile, eos, nullptr, nullptr, 0, 0, 0, per_sm, true, nullptr, 0);
+  const int none[2] = {0, 0};
+  return batch_pair_dispatch(precision, tile, eos, nullptr, nullptr, 0, nullptr, none, 0, 0, per_sm, true, nullptr, 0);
 }
 
 cudaError_t launch_batch_pair(int precision, int eos, int tile, const BatchBox *boxes, const int4 *items, int nitems,
-                              int parity, int sms, const int per_sm[2], unsigned *err, cudaStream_t s) {
+                              const int *block_box, const int fused_blocks[2], int parity, int sms,
+                              const int per_sm[2], unsigned *err, cudaStream_t s) {
   int ps[2] = {per_sm[0], per_sm[1]};
-  return batch_pair_dispatch(precision, tile, eos, boxes, items, nitems, parity, sms, ps, false, err, s);
+  return batch_pair_dispatch(precision, tile, eos, boxes, items, nitems, block_box, fused_blocks, parity, sms, ps,
+                             false, err, s);
 }
 
 cudaError_t launch_psi_pair(const KParams &P, int precision, const void *g, void *psi, unsigned *err,
