@@ -287,10 +287,11 @@ def e2e_run(op, prec, edge, steps):
     return t1 - t0, 8 * n, 32 * n
 
 
-def batched_run(steps, warmup, n_boxes=512):
+def batched_run(steps, warmup, n_boxes=512, tuning=None):
     """The batched workload: n_boxes periodic boxes (edges 32/48/64/96, every edge even), stepped as the
     autotuner picks: the work list (one launch per step) or the two-pass pair kernels (a flat fused grid per
-    operator, then the psi pass over work items: three launches per step)."""
+    operator, then the psi pass over work items: three launches per step).  tuning = (tile, z_planes) fixes the
+    choice instead (no autotuning launches: for launch lists)."""
     import torch
 
     from paper_1805_08643_gb300 import synth, thermo, tune
@@ -307,7 +308,12 @@ def batched_run(steps, warmup, n_boxes=512):
                         T=sp.T_over_Tc * Tc, G=G, rates=Rates(**RATES), sigma=SIGMA_DROPLET)
         batch.init_droplet(box, (sp.edge / 2,) * 3, sp.radius, W_DROPLET, rl, rv)
         nodes += sp.edge ** 3
-    tile, zc, table = tune.tune_batch(batch)
+    if tuning is None:
+        tile, zc, table = tune.tune_batch(batch)
+    else:
+        (tile, zc), table = tuning, {}
+        for box in batch.grids:
+            batch.set_tuning(tile, box, zc)
     steps += steps % 2
     batch.step(max(2, warmup + warmup % 2))
     stream = batch.stream
@@ -718,6 +724,8 @@ def main():
                     help="run a study instead of the benchmark line (minutes)")
     ap.add_argument("--study-steps", type=int, default=5000)
     ap.add_argument("--serve-jobs", type=int, default=200, help="jobs per offered rate of --study serve")
+    ap.add_argument("--batch-tuning", default=None,
+                    help="TILE,Z: fixed step kind and z planes of the batched form (default: autotuned)")
     ap.add_argument("--serve-capacity", type=float, default=None,
                     help="service capacity (jobs/s) of --study serve; default: measure it with a pilot")
     ap.add_argument("--serve-loads", default="0.25,0.5,1,1.5,2",
@@ -814,7 +822,8 @@ def main():
                                                         hbm_peak, field="flat")
 
     if args.forms in ("all", "batched"):
-        forms[f"batched_{args.batch_boxes}"] = batched_run(args.steps, args.warmup, args.batch_boxes)
+        bt = tuple(int(v) for v in args.batch_tuning.split(",")) if args.batch_tuning else None
+        forms[f"batched_{args.batch_boxes}"] = batched_run(args.steps, args.warmup, args.batch_boxes, bt)
         forms["served"] = served_run()
 
     e2e = None
