@@ -163,9 +163,8 @@ lbm_status rebuild(lbm_batch *b) {
     for (size_t k = 0; k < even.size(); ++k) {
       BatchBox &d = b->boxes[even[k].second].d;
       d.qbase = base[k];
-      d.tw = lbm::batch_tile_width(d.P.nx);
-      desc[even[k].second].qbase = d.qbase;
-      desc[even[k].second].tw = d.tw;
+      lbm::batch_queue_geometry(d);
+      desc[even[k].second] = d;
     }
     // the list numbers boxes in `even`; the kernel reads the descriptor table by slot: renumber, then
     // check every job against the descriptor it will read (plane and tile inside that box, counter

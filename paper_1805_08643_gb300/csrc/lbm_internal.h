@@ -148,6 +148,11 @@ struct alignas(16) BatchBox {  // 16-byte aligned: copied to shared memory in 16
   int qbase;  // first completion counter of this box in the batch work list, or (two-pass step) its first
               // block of the flat fused grid
   int tw;     // its tile width there (batch_tile_width)
+  // the rest of its work-list tile geometry (batch_queue_geometry): tiles along x and y and per plane, tile
+  // height, log2 of the node pairs across a tile, and ntx_m = ceil(2^32 / ntx), so that t / ntx is
+  // (t * ntx_m) >> 32 for every tile index t < 2^16
+  int ntx, nty, T, th, hshift;
+  unsigned long long ntx_m;
 };
 
 // Persistent single-pass launch over the work items (box, tx | ty << 16, z0, z1)
@@ -229,6 +234,7 @@ cudaError_t launch_queue(const KParams &P, int precision, int op, bool sigma, bo
 bool batch_queue_items(const std::vector<const KParams *> &boxes, int grid, std::vector<int4> &out,
                        std::vector<int> &base, long long *ncounters);
 int batch_tile_width(int nx);               // 64, 32 or 16: tiles of tw x (256 / tw) nodes
+void batch_queue_geometry(BatchBox &d);     // sets d.tw and the geometry fields from d.P
 int batch_queue_tiles(const KParams &P);   // tile jobs per plane of a box in a batch work list
 cudaError_t batch_queue_grid(int precision, int eos, int *grid);
 cudaError_t launch_batch_queue(int precision, int eos, const BatchBox *boxes, const int4 *items, int nitems,

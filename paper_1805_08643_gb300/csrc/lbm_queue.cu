@@ -215,6 +215,12 @@ __host__ __device__ inline BatchGeo batch_geo(const KParams &P, int tw) {
   return g;
 }
 
+// Tile row of tile t of a box: t / ntx by a multiply with the descriptor's
+// ceil(2^32 / ntx) instead of a division (exact for t * ntx < 2^32).
+__device__ __forceinline__ int tile_row(int t, const BatchBox &B) {
+  return (int)(((unsigned long long)(unsigned)t * B.ntx_m) >> 32);
+}
+
 // Copy box descriptors to shared memory with asynchronous 16-byte copies (one
 // commit group per call), so that the next item's descriptors arrive while the
 // current item runs.
@@ -255,11 +261,11 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
     if (it.x >= 0) {
       const BatchBox &B = bb[i & 1][0];
       const KParams &P = B.P;
-      const BatchGeo G = batch_geo(P, B.tw);
       int z = (int)((unsigned)it.y & 0xffffu), t = (int)((unsigned)it.y >> 16);
       asm volatile("" : "+r"(z), "+r"(t));
-      const int in = B.cur ^ parity, half = G.tw / 2;
-      const int x = (t % G.ntx) * G.tw + 2 * (tid % half), y = (t / G.ntx) * G.th + tid / half;
+      const int in = B.cur ^ parity;
+      const int ty = tile_row(t, B), tx = t - ty * B.ntx;
+      const int x = tx * B.tw + 2 * (tid & ((1 << B.hshift) - 1)), y = ty * B.th + (tid >> B.hshift);
       if (x < P.nx && y < P.ny) {
         const S *gi = (const S *)B.g[in];
         S *go = (S *)B.g[in ^ 1];
@@ -269,22 +275,21 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
           fused_pair_at<S, kOrth, true, false>(gi, go, B.psi[in], P, x, y, z, Rates<V2>(P));
       }
       __syncthreads();
-      if (tid == 0) counter_release_add(done + LBM_IDX(B.qbase + z * G.T + t, ndone), 1);
+      if (tid == 0) counter_release_add(done + LBM_IDX(B.qbase + z * B.T + t, ndone), 1);
     }
     if (it.z >= 0) {
       const BatchBox &B = bb[i & 1][1];
       const KParams &P = B.P;
-      const BatchGeo G = batch_geo(P, B.tw);
       int z = (int)((unsigned)it.w & 0xffffu), t = (int)((unsigned)it.w >> 16);
       asm volatile("" : "+r"(z), "+r"(t));
-      const int tx = t % G.ntx, ty = t / G.ntx, lane = threadIdx.x;
+      const int ty = tile_row(t, B), tx = t - ty * B.ntx, lane = threadIdx.x;
       bool ok = true;
       if (lane < 27) {  // fused jobs of planes z-1..z+1 on the 3 x 3 tiles around (tx, ty)
         int zz = z + lane / 9 - 1, xx = tx + lane % 3 - 1, yy = ty + (lane / 3) % 3 - 1;
         zz = zz < 0 ? zz + P.nz : (zz >= P.nz ? zz - P.nz : zz);
-        xx = xx < 0 ? xx + G.ntx : (xx >= G.ntx ? xx - G.ntx : xx);
-        yy = yy < 0 ? yy + G.nty : (yy >= G.nty ? yy - G.nty : yy);
-        const int *c = done + LBM_IDX(B.qbase + zz * G.T + yy * G.ntx + xx, ndone);
+        xx = xx < 0 ? xx + B.ntx : (xx >= B.ntx ? xx - B.ntx : xx);
+        yy = yy < 0 ? yy + B.nty : (yy >= B.nty ? yy - B.nty : yy);
+        const int *c = done + LBM_IDX(B.qbase + zz * B.T + yy * B.ntx + xx, ndone);
         const int target = 1 + P.wait_bias;  // counters are cleared before every launch
         for (int n = 0; counter_acquire(c) < target; ++n) {
           if (n >= P.spin_limit) {
@@ -295,8 +300,8 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
         }
       }
       if (!__all_sync(0xffffffffu, ok)) e |= kErrTimeout;
-      const int in = B.cur ^ parity, half = G.tw / 2;
-      const int x = tx * G.tw + 2 * (tid % half), y = ty * G.th + tid / half;
+      const int in = B.cur ^ parity;
+      const int x = tx * B.tw + 2 * (tid & ((1 << B.hshift) - 1)), y = ty * B.th + (tid >> B.hshift);
       if (x < P.nx && y < P.ny) psi_pair_at_l2<S, EOS, false, kIntCvt>((const S *)B.g[in ^ 1], B.psi[in ^ 1], P, x, y, z, e);
     }
     it = next;
@@ -436,6 +441,17 @@ int batch_tile_width(int nx) {
 }
 
 int batch_queue_tiles(const KParams &P) { return batch_geo(P, batch_tile_width(P.nx)).T; }
+
+void batch_queue_geometry(BatchBox &d) {
+  d.tw = batch_tile_width(d.P.nx);
+  const BatchGeo G = batch_geo(d.P, d.tw);
+  d.ntx = G.ntx;
+  d.nty = G.nty;
+  d.T = G.T;
+  d.th = G.th;
+  d.hshift = d.tw == 64 ? 5 : (d.tw == 32 ? 4 : 3);  // log2 of the node pairs across a tile
+  d.ntx_m = ((1ull << 32) + (unsigned long long)G.ntx - 1) / (unsigned long long)G.ntx;
+}
 
 bool batch_queue_items(const std::vector<const KParams *> &boxes, int grid, std::vector<int4> &out,
                        std::vector<int> &base, long long *ncounters) {
