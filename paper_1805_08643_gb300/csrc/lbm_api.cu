@@ -377,12 +377,14 @@ lbm_status lbm_step(lbm_ctx *c, int n) {
     void *gin = c->g[c->cur], *gout = c->g[c->cur ^ 1];
     if (c->queued) {
       void *pin = cur_psi(c), *pout = psi_at(c, c->pc ^ 1);
-      const int stamp = ++c->q_stamp;
+      // the counters advance only with launches that run (each one claims every item once)
+      const int stamp = c->q_stamp + 1;
       CK(timed(c, 1, [&] {
            return lbm::launch_queue(c->P, c->precision, c->op, c->sigma_on, c->eos_f2, gin, gout, pin, pout, c->q,
                                     stamp, err_word(c), c->L.stream);
          }),
          "single-pass kernel");
+      c->q_stamp = stamp;
       c->pc ^= 1;
       c->cur ^= 1;
       c->psi_valid = true;

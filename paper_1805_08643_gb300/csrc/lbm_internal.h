@@ -207,9 +207,9 @@ cudaError_t launch_lagged(const KParams &P, int precision, int op, bool sigma, b
 // Single-pass step on an ordered work list (FP32 arithmetic, D3Q19, Nx even):
 // items of a fused tile job and a lagging psi tile job, one cooperative launch
 // of `grid` blocks (queue_grid) working through the list queue_items builds
-// (and checks: false if it cannot).  The device side: the item table and a
-// completion counter per fused job (queue_counters ints, zero before the
-// first launch).
+// (and checks: false if it cannot).  The device side: the item table, a
+// completion counter per fused job and the blocks' item-claim counter
+// (queue_counters ints, zero before the first launch).
 struct QueueState {
   const int4 *items;
   int nitems;

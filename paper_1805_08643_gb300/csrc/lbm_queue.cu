@@ -16,12 +16,20 @@
 // reaches the psi job those fused jobs are normally finished, so the wait is
 // one poll, while writer and reader stay close enough for the populations to
 // be still in L2 (measured on GB300: a whole wave waits less but re-reads about
-// twice as much from DRAM, and is slower; a quarter waits more).  Block b works through items b, b + grid, b + 2 grid, ...; the
-// launch is cooperative (every block resident), so the unfinished item with
-// the lowest index always has its block at it and waits only on earlier fused
-// jobs, which are finished: progress needs no timing assumption.  Waits are
-// bounded all the same (KParams::spin_limit; a wait that gives up sets
-// kErrTimeout and the launch still ends).
+// twice as much from DRAM, and is slower; a quarter waits more).
+//
+// Block b starts with item b; from then on it claims the next unclaimed item
+// (one atomic fetch per item, issued when an item starts and read when it
+// ends), so blocks take items in list order whatever their speed.  (With the
+// static order b, b + grid, ..., blocks drifted up to five items apart within
+// a wave, and the psi jobs of the fast ones waited on the slow ones: 0.556
+// against 0.528 ms per 256^3 step on GB300.)  Claims are in increasing order
+// and the launch is cooperative (every block resident): a block holding an
+// unfinished fused job is busy with an earlier item, so the psi job of the
+// lowest unfinished item waits only on fused jobs that are finished or
+// running, and progress needs no timing assumption.  Waits are bounded all
+// the same (KParams::spin_limit; a wait that gives up sets kErrTimeout and
+// the launch still ends).
 //
 // What this buys over two launches: the psi jobs' FP64 EOS runs on the same
 // SMs while the fused jobs stream HBM, and the populations they pull come from
@@ -33,6 +41,10 @@
 // Counters: done[z * T + tile] counts the launches in which fused job
 // (z, tile) has finished (one release increment after a block barrier), so a
 // psi job of launch `stamp` waits for done >= stamp and nothing is ever reset.
+// done[nz * T + 16] counts the item claims: exactly nitems per launch (one
+// for every item a block runs; the one made during a block's last item names
+// no item), so launch `stamp` claims numbers (stamp - 1) * nitems onwards,
+// modulo 2^32.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -68,6 +80,18 @@ __host__ __device__ inline TileGeo tile_geo(const KParams &P) {
   return g;
 }
 
+// The item claim number c of this launch names: gridDim.x + c.  Every launch
+// makes exactly nitems claims, so c < nitems; a claim outside that range
+// (claim counter and launch count out of step) ends the block's loop and is
+// reported as a timeout: the list could not be followed.
+__device__ __forceinline__ int next_item(unsigned c, int nitems, unsigned &e) {
+  if (c >= (unsigned)nitems) {
+    e |= kErrTimeout;
+    return nitems;
+  }
+  return (int)gridDim.x + (int)c;
+}
+
 // item: x = fused plane (or -1), y = its tile, z = psi plane (or -1), w = its tile.
 // Q: 19 (both operators) or 15 (the D3Q15 non-orthogonal variant).
 template <typename S, int OP, bool SIGMA, int EOS, bool DF, int Q>
@@ -78,8 +102,14 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
   const TileGeo G = tile_geo(P);
   const int lane = threadIdx.x, row = threadIdx.y;
   unsigned e = 0;
+  __shared__ int s_next;
+  unsigned *claims = (unsigned *)(done + P.nz * G.T + 16);
+  const unsigned base = (unsigned)(stamp - 1) * (unsigned)nitems;
+  int k = blockIdx.x;
 #pragma unroll 1
-  for (int k = blockIdx.x; k < nitems; k += gridDim.x) {
+  while (k < nitems) {
+    unsigned claim = 0;
+    if (lane == 0 && row == 0) claim = atomicAdd(claims, 1u);  // the next item: gridDim.x + claim - base
     const int4 it = __ldg(items + k);
     if (it.x >= 0) {
       int z = it.x, t = it.y;
@@ -91,9 +121,14 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
         else
           fused_pair_at<S, OP, SIGMA, false>(g_in, g_out, psi_in, P, x, y, z, Rates<V2>(P));
       }
+      if (lane == 0 && row == 0) s_next = next_item(claim - base, nitems, e);
       __syncthreads();
       if (lane == 0 && row == 0) counter_release_add(done + LBM_IDX(z * G.T + t, P.nz * G.T), 1);
+    } else {
+      if (lane == 0 && row == 0) s_next = next_item(claim - base, nitems, e);
+      __syncthreads();
     }
+    const int kn = s_next;  // read before the next item's barrier, rewritten only after it
     if (it.z >= 0) {
       int z = it.z, t = it.w;
       asm volatile("" : "+r"(z), "+r"(t));
@@ -123,6 +158,7 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
           psi_pair_at_l2<S, EOS, DF, kIntCvt>(g_out, psi_out, P, x, y, z, e);
       }
     }
+    k = kn;
   }
   if (e) atomicOr(err, e);
 }
@@ -364,7 +400,7 @@ cudaError_t queue_grid(int precision, int *grid) {
   return cudaSuccess;
 }
 
-size_t queue_counters(const KParams &P) { return (size_t)P.nz * tile_geo(P).T; }
+size_t queue_counters(const KParams &P) { return (size_t)P.nz * tile_geo(P).T + 32; }  // + the claim counter
 
 bool queue_items(const KParams &P, int grid, std::vector<int4> &out) {
   const TileGeo G = tile_geo(P);
