@@ -146,10 +146,16 @@ lbm_status lbm_init_flat(lbm_ctx *ctx, int axis, double lo, double hi, double W,
 lbm_status lbm_init_field(lbm_ctx *ctx, const double *rho, int on_device, double rho_ref);
 
 /* Advance n >= 1 time steps (asynchronous on the context's stream).  Each step
- * is two kernels: the psi pass and the fused force + collision + pull-streaming
- * pass.  Errors: LBM_ERR_ARG (n < 1), LBM_ERR_STATE (no init), LBM_ERR_CUDA;
- * LBM_ERR_EOS_DOMAIN / LBM_ERR_NONFINITE when a check interval is set (below)
- * and a check inside this call fails. */
+ * is the form's step kernels (lbm_set_tuning): by default, for FP32 storage
+ * with an even Nx, one cooperative launch of the work-list single pass;
+ * otherwise two kernels, the psi pass and the fused force + collision +
+ * pull-streaming pass.  A work-list launch carries the context's launch count
+ * (its completion and item-claim counters advance with every launch), so steps
+ * must not be captured into a CUDA graph and replayed: a replayed launch finds
+ * its counters out of step, stops early and reports LBM_ERR_TIMEOUT at the next
+ * check.  Errors: LBM_ERR_ARG (n < 1), LBM_ERR_STATE (no init), LBM_ERR_CUDA;
+ * LBM_ERR_EOS_DOMAIN / LBM_ERR_NONFINITE / LBM_ERR_TIMEOUT when a check
+ * interval is set (below) and a check inside this call fails. */
 lbm_status lbm_step(lbm_ctx *ctx, int n);
 
 /* Density rho (N doubles) and velocity u (3N doubles, u_x block then u_y then
@@ -168,8 +174,9 @@ lbm_status lbm_diag(lbm_ctx *ctx, double out[5]);
 
 /* Read and clear the device error word set by the kernels (synchronises):
  * LBM_OK, LBM_ERR_EOS_DOMAIN, LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT (a bounded
- * wait of a single-pass kernel gave up) or, in the debug build of the library
- * (compiled with LBM_BOUNDS_CHECK), LBM_ERR_BOUNDS. */
+ * wait of a single-pass kernel gave up, or a work-list launch could not follow
+ * its list) or, in the debug build of the library (compiled with
+ * LBM_BOUNDS_CHECK), LBM_ERR_BOUNDS. */
 lbm_status lbm_check(lbm_ctx *ctx);
 
 /* Make lbm_step run lbm_check every k steps (0, the default, never). */

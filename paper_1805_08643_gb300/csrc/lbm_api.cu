@@ -350,7 +350,8 @@ lbm_status lbm_check(lbm_ctx *c) {
   CK(cudaMemsetAsync(err_word(c), 0, sizeof(unsigned), c->L.stream), "clear error word");
   CK(cudaStreamSynchronize(c->L.stream), "cudaStreamSynchronize");
   if (lbm::dbg::take_all()) return fail(c, LBM_ERR_BOUNDS, "a kernel index fell outside its buffer (debug build)");
-  if (w & lbm::kErrTimeout) return fail(c, LBM_ERR_TIMEOUT, "a bounded wait gave up");
+  if (w & lbm::kErrTimeout)
+    return fail(c, LBM_ERR_TIMEOUT, "a bounded wait gave up, or a work-list launch could not follow its list");
   if (w & lbm::kErrNonFinite) return fail(c, LBM_ERR_NONFINITE, "non-finite density");
   if (w & lbm::kErrEosDomain) return fail(c, LBM_ERR_EOS_DOMAIN, "density left the domain of the EOS");
   return LBM_OK;
