@@ -337,7 +337,7 @@ def batched_run(steps, warmup, n_boxes=512, tuning=None):
             "physics": "a=0.25, W=5, sigma=0.105, T/Tc~U[0.6,0.9], R~U[6,edge/3], FP32"}
 
 
-def served_run(n_jobs=24, load=1.0, max_steps=2000, tol=1e-7):
+def served_run(n_jobs=24, load=1.0, max_steps=20000, tol=1e-7):
     """The served workload, scaled down: Poisson droplet / slab jobs, edges U[48, 96], continuous batching."""
     from paper_1805_08643_gb300 import synth
     from paper_1805_08643_gb300.serve import BatchBackend, Server

@@ -102,6 +102,9 @@ size_t box_bytes(int precision, long long n) {
   return 2 * up(pop) + 2 * up((size_t)n * 4) + up((size_t)3 * n * 4);
 }
 
+// Ints after a work list's completion counters for the blocks' item-claim counter (at offset 16).
+constexpr long long kClaimInts = 32;
+
 // Planes per work item unless tuned: 32 (two of them are recomputed).
 int default_zc(const KParams &P) { return std::min(P.nz, 32); }
 
@@ -184,11 +187,11 @@ lbm_status rebuild(lbm_batch *b) {
           return bfail(b, LBM_ERR_ARG, "work list does not match the box table");
       }
     }
-    if (nc > b->cap_done) {
+    if (nc + kClaimInts > b->cap_done) {  // the counters, then the blocks' item-claim counter
       if (b->d_done) cudaFreeAsync(b->d_done, b->stream);
       b->d_done = nullptr;
-      BCK(cudaMallocAsync((void **)&b->d_done, sizeof(int) * std::max(nc, 1LL), b->stream), "work list counters");
-      b->cap_done = nc;
+      BCK(cudaMallocAsync((void **)&b->d_done, sizeof(int) * (nc + kClaimInts), b->stream), "work list counters");
+      b->cap_done = nc + kClaimInts;
     }
     b->ndone = nc;
   } else {
@@ -249,7 +252,7 @@ lbm_status rebuild(lbm_batch *b) {
     auto step = [&](int parity) {
       cudaError_t e = cudaSuccess;
       if (wl) {
-        e = cudaMemsetAsync(b->d_done, 0, sizeof(int) * (size_t)b->ndone, b->stream);
+        e = cudaMemsetAsync(b->d_done, 0, sizeof(int) * (size_t)(b->ndone + kClaimInts), b->stream);
         if (e == cudaSuccess)
           e = lbm::launch_batch_queue(b->precision, b->eos, b->d_boxes, b->d_items, n_even, parity, b->wl_grid,
                                       b->d_done, (int)b->ndone, b->d_err, b->stream);

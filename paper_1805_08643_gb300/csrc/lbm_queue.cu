@@ -260,7 +260,8 @@ __device__ __forceinline__ int tile_row(int t, const BatchBox &B) {
 // Copy box descriptors to shared memory with asynchronous 16-byte copies (one
 // commit group per call), so that the next item's descriptors arrive while the
 // current item runs.
-__device__ __forceinline__ void prefetch_boxes(BatchBox *dst, const BatchBox *__restrict__ boxes, int4 it, int tid) {
+__device__ __forceinline__ void prefetch_boxes(BatchBox *dst, const BatchBox *__restrict__ boxes, int4 it, int tid,
+                                               int nthreads = NTH) {
   constexpr int chunks = (int)(sizeof(BatchBox) / 16);
   static_assert(sizeof(BatchBox) % 16 == 0, "descriptor copies move 16-byte pieces");
   for (int side = 0; side < 2; ++side) {
@@ -268,7 +269,7 @@ __device__ __forceinline__ void prefetch_boxes(BatchBox *dst, const BatchBox *__
     if (box < 0) continue;
     const char *src = (const char *)(boxes + box);
     char *d = (char *)(dst + side);
-    for (int c = tid; c < chunks; c += NTH) {
+    for (int c = tid; c < chunks; c += nthreads) {
       const unsigned sa = (unsigned)__cvta_generic_to_shared(d + 16 * c);
       asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(src + 16 * c) : "memory");
     }
@@ -283,16 +284,19 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
   __shared__ BatchBox bb[2][2];  // [item parity][fused job's box, psi job's box]
   const int tid = threadIdx.y * TXP + threadIdx.x;
   unsigned e = 0;
+  // block b starts with item b, then claims the next unclaimed item (one atomic fetch per item, issued
+  // when an item starts); warp 0 reads the claimed item and copies its descriptors during the psi job
+  __shared__ int s_next;
+  __shared__ int4 s_it;
+  unsigned *claims = (unsigned *)(done + ndone + 16);  // cleared with the counters before every launch
   int k = blockIdx.x;
   int4 it = k < nitems ? __ldg(items + k) : make_int4(-1, -1, -1, -1);
   prefetch_boxes(bb[0], boxes, it, tid);
 #pragma unroll 1
-  for (int i = 0; k < nitems; ++i, k += gridDim.x) {
-    const int kn = k + gridDim.x;
-    const int4 next = kn < nitems ? __ldg(items + kn) : make_int4(-1, -1, -1, -1);
-    __syncthreads();  // every thread is done with the buffer the next copies overwrite
-    prefetch_boxes(bb[(i + 1) & 1], boxes, next, tid);
-    asm volatile("cp.async.wait_group 1;" ::: "memory");  // this item's descriptors have arrived
+  for (int i = 0; k < nitems; ++i) {
+    unsigned claim = 0;
+    if (tid == 0) claim = atomicAdd(claims, 1u);  // the next item: gridDim.x + claim
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // this item's descriptors have arrived
     __syncthreads();
     if (it.x >= 0) {
       const BatchBox &B = bb[i & 1][0];
@@ -312,6 +316,15 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
       }
       __syncthreads();
       if (tid == 0) counter_release_add(done + LBM_IDX(B.qbase + z * B.T + t, ndone), 1);
+    }
+    if (threadIdx.y == 0) {  // the next item and its descriptors (buffer (i + 1) & 1 was item i - 1's)
+      const int kn = (int)min((unsigned)gridDim.x + __shfl_sync(0xffffffffu, claim, 0), (unsigned)nitems);
+      const int4 nx = kn < nitems ? __ldg(items + kn) : make_int4(-1, -1, -1, -1);
+      prefetch_boxes(bb[(i + 1) & 1], boxes, nx, threadIdx.x, TXP);
+      if (threadIdx.x == 0) {
+        s_next = kn;
+        s_it = nx;
+      }
     }
     if (it.z >= 0) {
       const BatchBox &B = bb[i & 1][1];
@@ -340,7 +353,9 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
       const int x = tx * B.tw + 2 * (tid & ((1 << B.hshift) - 1)), y = ty * B.th + (tid >> B.hshift);
       if (x < P.nx && y < P.ny) psi_pair_at_l2<S, EOS, false, kIntCvt>((const S *)B.g[in ^ 1], B.psi[in ^ 1], P, x, y, z, e);
     }
-    it = next;
+    __syncthreads();  // s_next and s_it are written; rewritten only after the next item's first barrier
+    k = s_next;
+    it = s_it;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the block
   if (e) atomicOr(err, e);
