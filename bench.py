@@ -23,7 +23,7 @@ bracketed by CUDA events on the launch stream with nothing else recorded inside
 (the kernel split comes from a separate region with per-launch events).
 
   python bench.py [--gpus N --steps K --warmup W --repeats R] [--impl reference]
-                  [--forms headline|batched|all] [--op nonorth|orth|nonorth_d3q15] [--prec f64|f32|f16]
+                  [--forms headline|batch|batched|all] [--op nonorth|orth|nonorth_d3q15] [--prec f64|f32|f16]
                   [--mode default|two-pass|queue|lagged|onchip|single|tma]
 
 Under torchrun (N > 1) each rank runs its own box on its own GPU (replicas,
@@ -714,7 +714,8 @@ def main():
     ap.add_argument("--mode", default="default", choices=sorted(MODES),
                     help="step kernels: the library default (work-list single pass for FP32 storage, two-pass "
                          "otherwise), or one of the lbm_set_tuning modes")
-    ap.add_argument("--forms", default="all", help="'all', 'headline' or 'batched' (headline + batched + served)")
+    ap.add_argument("--forms", default="all",
+                    help="'all', 'headline', 'batched' (headline + batched + served) or 'batch' (headline + batched)")
     ap.add_argument("--batch-boxes", type=int, default=512, help="boxes of the batched form")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -821,9 +822,10 @@ def main():
             forms[f"nonorth_{fprec}_flat"] = form_entry("nonorth", fprec, E, k64 if fprec == "f64" else K, W, world,
                                                         hbm_peak, field="flat")
 
-    if args.forms in ("all", "batched"):
+    if args.forms in ("all", "batched", "batch"):
         bt = tuple(int(v) for v in args.batch_tuning.split(",")) if args.batch_tuning else None
         forms[f"batched_{args.batch_boxes}"] = batched_run(args.steps, args.warmup, args.batch_boxes, bt)
+    if args.forms in ("all", "batched"):
         forms["served"] = served_run()
 
     e2e = None
