@@ -201,3 +201,30 @@ def test_d3q15_work_list_against_its_oracle():
     f0 = D.equilibrium_state(p, droplet_rho(grid, centre, 6.0, 2.0, rl, rv))
     rho_o, u_o, _, _ = D.macroscopic(p, D.run(p, f0, steps))
     assert max_abs(rho, rho_o) <= 2e-5 and max_abs(u, u_o) <= 2e-5
+
+
+def test_queue_claims_stay_in_step_across_mode_switches_and_inits():
+    """Blocks claim work-list items from a counter that advances with every launch: switching to the two-pass
+    step and back, re-initialising, and steps in chunks of 1, 2 and 5 must leave every launch claiming its own
+    items (bit-exact with the two-pass step, no LBM_ERR_TIMEOUT)."""
+    grid = (32, 16, 12)
+    rl, rv = coexistence(0.8)
+    lat = lattice(grid, "nonorth", "f32", physics(sigma=0.105))
+    lat.set_tuning("queue", 1, 0)
+    lat.init_droplet((16.0, 8.0, 6.0), 4.0, 2.0, rl, rv)
+    for n in (1, 2, 5):
+        lat.step(n)
+    lat.set_tuning(False, 1, 0)
+    lat.step(3)
+    lat.set_tuning("queue", 1, 0)
+    lat.step(4)
+    assert lat.check() == 0
+    got = lat.moments(), lat.populations()
+    lat.init_droplet((16.0, 8.0, 6.0), 4.0, 2.0, rl, rv)  # a new run on the same counters
+    lat.step(15)
+    assert lat.check() == 0
+    again = lat.moments(), lat.populations()
+    lat.close()
+    _, ref = _run(grid, "nonorth", "f32", False, 15, sigma=0.105, R=4.0)
+    assert _equal(ref, got)
+    assert _equal(ref, again)
