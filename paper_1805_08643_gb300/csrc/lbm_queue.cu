@@ -102,10 +102,14 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
   const TileGeo G = tile_geo(P);
   const int lane = threadIdx.x, row = threadIdx.y;
   unsigned e = 0;
-  __shared__ int s_next;
+  // the claimed next item, by item parity: thread 0 writes slot i & 1 before item i's barrier and the block
+  // reads it after that barrier; the slot is written again two items later, after every thread has passed
+  // item i + 1's barrier
+  __shared__ int s_next[2];
   unsigned *claims = (unsigned *)(done + P.nz * G.T + 16);
   const unsigned base = (unsigned)(stamp - 1) * (unsigned)nitems;
   int k = blockIdx.x;
+  int par = 0;
 #pragma unroll 1
   while (k < nitems) {
     unsigned claim = 0;
@@ -121,14 +125,15 @@ __global__ void __launch_bounds__(NTH, kMinBlocks)
         else
           fused_pair_at<S, OP, SIGMA, false>(g_in, g_out, psi_in, P, x, y, z, Rates<V2>(P));
       }
-      if (lane == 0 && row == 0) s_next = next_item(claim - base, nitems, e);
+      if (lane == 0 && row == 0) s_next[par] = next_item(claim - base, nitems, e);
       __syncthreads();
       if (lane == 0 && row == 0) counter_release_add(done + LBM_IDX(z * G.T + t, P.nz * G.T), 1);
     } else {
-      if (lane == 0 && row == 0) s_next = next_item(claim - base, nitems, e);
+      if (lane == 0 && row == 0) s_next[par] = next_item(claim - base, nitems, e);
       __syncthreads();
     }
-    const int kn = s_next;  // read before the next item's barrier, rewritten only after it
+    const int kn = s_next[par];
+    par ^= 1;
     if (it.z >= 0) {
       int z = it.z, t = it.w;
       asm volatile("" : "+r"(z), "+r"(t));
